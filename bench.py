@@ -1,0 +1,321 @@
+"""Benchmark: time to a 1e-10 relative residual (hence backward error <= 1e-10)
+of mixed-precision GADI (FP64 outer, FP32 inner) against plain FP64 GADI on
+the same GPU, on 2D convection-diffusion -Lap u + beta.grad u, 5-point
+centred differences on a 2048 x 2048 interior grid (n = 4,194,304), beta drawn
+from U[1,100]^2 by seed, b = A x_true with x_true ~ U[0,1).
+
+One step = one complete mixed-precision solve from x_0 = 0 to the tolerance
+(every step of Algorithm 1: residual, H-solve, S-solve, update, stopping
+test), inputs resident in HBM, timed with CUDA events on the solve's stream.
+The L2 cache is flushed (a 256 MB buffer is written) before each step.
+Printed as one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (a bounded sample, see `cpu_baseline`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "conv-diff-2d 2048x2048 (n=4194304), beta~U[1,100]^2 seed 2, HSS, tol 1e-10"
+# GADI parameters shared by the mixed and the plain FP64 runs
+ALPHA_FACTOR = 4.0     # alpha = ALPHA_FACTOR * alpha* (closed-form HSS value)
+OMEGA = 0.0
+TOL = 1e-10
+MAXIT = 20000
+TOL_INNER = 1e-3
+HBM_FALLBACK = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+        self.out = ""
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n: int, stats: dict, s_bytes: int, d_bytes: int = 8) -> float:
+    """Bytes the method must move for one solve (per point: outer residual +
+    update 3d+2s, each CG iteration on H 8s, each CGNR iteration on S 8s, the
+    CGNR set-up S^T g 2s)."""
+    k = stats["outer_its"]
+    per_pt = (k + 1) * (3 * d_bytes + 2 * s_bytes) + 8 * s_bytes * (stats["inner_its_h"] + stats["inner_its_s"]) \
+        + 2 * s_bytes * k
+    return float(n) * per_pt
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import alpha_star, config2
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+    p, xt = config2(args.n)
+    alpha = ALPHA_FACTOR * alpha_star(p)
+    n = p.nvec
+    H = G.Gadi.from_problem(p)
+    stream = torch.cuda.current_stream()
+    xtd = torch.from_numpy(xt).cuda()
+    b = torch.zeros_like(xtd)
+    H.apply(G.OP_A, xtd, b)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kw = dict(tol_h=TOL_INNER, tol_s=TOL_INNER)
+
+    def one(prec):
+        x.zero_()
+        flush.zero_()
+        st, s = H.solve(b, x, alpha, OMEGA, prec, TOL, args.maxit, **kw)
+        return st, s
+
+    for _ in range(args.warmup):
+        one(G.FP32)
+    # timed region: K mixed-precision solves
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_s, per = [], []
+    with Clocks(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.time()
+        for _ in range(args.steps):
+            flush.zero_()
+            x.zero_()
+            ev0.record(stream)
+            st, s = H.solve(b, x, alpha, OMEGA, G.FP32, TOL, args.maxit, **kw)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            per.append(ev0.elapsed_time(ev1) / 1e3)
+            kern_s.append(s["seconds"])
+        torch.cuda.synchronize()
+        t_wall = time.time() - t_wall
+    if world > 1:
+        t = torch.tensor([max(per)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mixed_stats, mixed_status = s, st
+    # check the answer: FP64 residual through the library's own operator
+    r = torch.zeros_like(b)
+    H.apply(G.OP_A, x, r)
+    relres = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+    anorm = H.norm2(50)
+    be = float(torch.linalg.norm(b - r) / (anorm * torch.linalg.norm(x) + torch.linalg.norm(b)))
+    fe = float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))
+
+    # plain FP64 GADI on the same GPU, same alpha/omega/tolerances
+    fp64 = None
+    if not args.skip_fp64:
+        one(G.FP64)  # warm-up
+        f_times = []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            x.zero_()
+            ev0.record(stream)
+            st64, s64 = H.solve(b, x, alpha, OMEGA, G.FP64, TOL, args.maxit, **kw)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            f_times.append(ev0.elapsed_time(ev1) / 1e3)
+        H.apply(G.OP_A, x, r)
+        fp64 = {"seconds": statistics.median(f_times), "status": G.status_str(st64),
+                "outer_its": s64["outer_its"], "inner_its_h": s64["inner_its_h"],
+                "inner_its_s": s64["inner_its_s"],
+                "relres": float(torch.linalg.norm(b - r) / torch.linalg.norm(b)),
+                "kernel_GBps": algorithmic_bytes(n, s64, 8) / s64["seconds"] / 1e9}
+
+    # end-to-end through the C ABI with host (pinned) buffers
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for i in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.solve(bh.numpy(), xh.numpy(), alpha, OMEGA, G.FP32, TOL, args.maxit, **kw)
+        e2e.append(time.perf_counter() - t0)
+
+    hbm, src = _peaks()
+    value = statistics.mean(per)
+    ab = algorithmic_bytes(n, mixed_stats, 4)
+    kmean = statistics.mean(kern_s)
+    achieved = ab / kmean / 1e9
+    out = {
+        "metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
+        "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 outer / f32 inner", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "alpha": alpha, "alpha_over_alpha_star": ALPHA_FACTOR,
+                   "omega": OMEGA, "tol_inner": TOL_INNER, "u_s": "fp32", "u": "fp64",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MB write) before each step"},
+        "status": G.status_str(mixed_status), "outer_its": mixed_stats["outer_its"],
+        "inner_its_h": mixed_stats["inner_its_h"], "inner_its_s": mixed_stats["inner_its_s"],
+        "relres": relres, "backward_error": be, "forward_error": fe,
+        "fp64_plain": fp64,
+        "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                     "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve)",
+                     "algorithmic_bytes": ab},
+        "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s": t_wall,
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(p, xt, alpha, mixed_stats, args.cpu_outer)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(p, xt, alpha, gpu_stats, outer):
+    """The CPU oracle timed on a bounded sample: `outer` outer iterations of
+    Algorithm 1 (FP64 outer, FP32 inner) on the full grid, scaled to the
+    number of outer iterations the mixed solve needed."""
+    import oracle as O
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    t0 = time.perf_counter()
+    _, st = orc.gadi(b, alpha, OMEGA, O.FP32, tol=0.0, maxit=outer, tol_h=TOL_INNER, tol_s=TOL_INNER,
+                     outer_stag_window=0)
+    dt = time.perf_counter() - t0
+    per_outer = dt / max(1, st["outer_its"])
+    k = gpu_stats["outer_its"]
+    return {"value": per_outer * k, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"{st['outer_its']} outer iterations of the C oracle (single thread) on the full "
+                      f"2048^2 grid in {dt:.1f} s, scaled by the {k} outer iterations of the mixed solve"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workloads import alpha_star, config2
+    p, xt = config2(args.n)
+    alpha = ALPHA_FACTOR * alpha_star(p)
+    counts = {"outer_its": args.ref_outer}
+    try:
+        with open(os.path.join(ROOT, "profiles", "bench_counts.json")) as f:
+            counts = json.load(f)
+    except Exception:
+        pass
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(p, xt, alpha, counts, 1)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    out = {"metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
+           "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 outer / f32 inner", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "alpha_over_alpha_star": ALPHA_FACTOR, "omega": OMEGA},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--maxit", type=int, default=MAXIT)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-outer", type=int, default=1)
+    ap.add_argument("--ref-outer", type=int, default=2800)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * gadi.h -- C ABI of the GB300 (sm_103a) implementation of three-precision
+ * General ADI (GADI) for sparse A x = b, following arXiv 2512.21164.
+ *
+ * The method (Algorithm 1 of the paper, Sec. 2.3): with the splitting
+ * A = M + N (Sec. 3.1, "eq:split"), a regularisation alpha > 0 and an
+ * extrapolation omega in [0, 2) (Sec. 1, Lemma 1), repeat
+ *     r = b - A x                               in u_r  (FP64 here)
+ *     solve (alpha I + M) z = r                 in u_s  (FP64, FP32 or BF16)
+ *     solve (alpha I + N) y = (2 - omega) alpha z   in u_s
+ *     x = x + y                                 in u    (FP64)
+ * until ||b - A x|| / ||b - A x_0|| <= tol.  The splitting is HSS:
+ * M = (A + A^T)/2, N = (A - A^T)/2, used for every problem class of Sec. 5.
+ * The shifted SPD system is solved by CG; the shifted skew system by CG on
+ * the normal equations (Sec. 5.1), or exactly and pointwise when alpha I + N
+ * is diagonal (the complex class of Sec. 5.4).
+ *
+ * Precisions (Sec. 3.1 requires u_r <= u <= u_s; Sec. 5.1 variants):
+ *   u = u_r = FP64 (u_high must be GADI_FP64);
+ *   u_s = u_low: FP64 (GADI-FP64), FP32 (GADI-FP32) or BF16 storage with FP32
+ *   arithmetic (GADI-BF16).  Inner vectors are stored in u_s; dot products and
+ *   matrix-vector products are carried in FP32 (FP64 when u_s = FP64).
+ *
+ * Conventions for every entry point below:
+ *   - Status: negative values are errors; on an error no output is written.
+ *     Positive values (NOT_CONVERGED, STAGNATED, DIVERGED) are non-fatal: x
+ *     holds the last iterate and the stats are filled.
+ *   - Pointers to vectors may be host or device memory of the current CUDA
+ *     device unless stated otherwise; the library detects which.  Host
+ *     vectors are staged through device buffers owned by the handle (the
+ *     copies are part of the call).
+ *   - Vectors have length n doubles for real problems and 2n doubles for the
+ *     complex class (interleaved re, im pairs), n = nx*ny(*nz) or the CSR size.
+ *   - Grids are row-major with x fastest: index (z*ny + y)*nx + x.
+ *   - Device vectors should start on a 16-byte boundary (any cudaMalloc or
+ *     PyTorch allocation does); real-valued vectors that do not are handled
+ *     by a slower path, complex ones are rejected with GADI_ERR_INVALID.
+ *   - Calls on one handle are not thread-safe.  All work is issued on the
+ *     stream given in gadi_opts (NULL = the legacy default stream) and the
+ *     calls return after that work has finished.
+ *   - The library never calls back into Python or PyTorch; device memory for
+ *     its own workspace comes from cudaMalloc in gadi_create / first solve.
+ */
+#ifndef GADI_H
+#define GADI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GADI_OK = 0,              /* converged: relres <= tol                      */
+    GADI_NOT_CONVERGED = 1,   /* maxit outer iterations reached                */
+    GADI_STAGNATED = 2,       /* relres fell < 1% over the stagnation window   */
+    GADI_DIVERGED = 3,        /* relres > 1e6 or not finite                    */
+    GADI_ERR_INVALID = -1,    /* bad argument                                  */
+    GADI_ERR_NONFINITE = -2,  /* NaN/Inf in an input vector or parameter       */
+    GADI_ERR_CUDA = -3,       /* a CUDA runtime call failed                    */
+    GADI_ERR_OOM = -4,        /* device allocation failed                      */
+    GADI_ERR_TIMEOUT = -5,    /* a device-side grid barrier gave up waiting    */
+    GADI_ERR_UNSUPPORTED = -6 /* valid request this build does not implement   */
+} gadi_status;
+
+typedef enum { GADI_FP64 = 0, GADI_FP32 = 1, GADI_BF16 = 2 } gadi_prec;
+
+/* Splittings of Sec. 2.1.  Only HSS is used by the paper's experiments
+ * (Sec. 5.2-5.4); the others are reserved. */
+typedef enum { GADI_SPLIT_HSS = 0 } gadi_splitting;
+
+/* Problem classes of Sec. 5, plus a general CSR matrix (Sec. 5.1: the
+ * paper's own implementation stores A, H and S as sparse matrices). */
+typedef enum {
+    GADI_STENCIL_2D5 = 0, /* -Lap u + beta.grad u, 5-point, Sec. 5.2          */
+    GADI_STENCIL_3D7 = 1, /* 3D convection-diffusion, 7-point, Sec. 5.3       */
+    GADI_COMPLEX_2D5 = 2, /* (L + kappa I) + i sigma I, Sec. 5.4              */
+    GADI_CSR = 3          /* general A with positive definite (A + A^T)/2     */
+} gadi_kind;
+
+/* Operators for gadi_apply. */
+typedef enum { GADI_OP_A = 0, GADI_OP_M = 1, GADI_OP_N = 2, GADI_OP_AT = 3 } gadi_op;
+
+/* Problem descriptor (Sec. 5.2-5.4).  Stencil matrices are the centred finite
+ * differences scaled by h^2 (entries O(1)):
+ *   2D: A = M + N, M: centre 4, neighbours -1; N: E +c_x, W -c_x, N +c_y,
+ *       S -c_y with c_i = beta_i h / 2;
+ *   3D: centre 6 and a third axis;
+ *   complex: M = L + kappa I (L the 5-point Laplacian), N = i sigma I.
+ * h <= 0 means h = 1/(nx+1).  CSR arrays (host memory, 0-based, int32 indices,
+ * FP64 values, n rows) are copied by gadi_create; the caller keeps them. */
+typedef struct {
+    int kind;
+    int nx, ny, nz;
+    double h;
+    double beta[3];
+    double kappa, sigma;
+    int n;
+    const int *rowptr;
+    const int *col;
+    const double *val;
+} gadi_problem;
+
+/* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2
+ * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
+ * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
+ * per SM), hist = NULL. */
+typedef struct {
+    double tol_h;          /* inner CG relative residual tolerance on H     */
+    double tol_s;          /* inner CGNR tolerance on S (normal residual)   */
+    int maxit_inner;       /* cap on each inner solve (reaching it is fine) */
+    int inner_stag;        /* stop an inner solve after this many steps
+                              without a new residual minimum (0 = off)      */
+    int outer_stag_window; /* STAGNATED if relres fell < 1% over this many
+                              outer iterations (0 = off)                    */
+    int s_pointwise;       /* complex class: solve the diagonal S exactly   */
+    void *stream;          /* cudaStream_t                                  */
+    int max_blocks;        /* cap on persistent blocks (0 = automatic)      */
+    double *hist;          /* optional HOST array of maxit+1 doubles: relres
+                              per outer iteration                           */
+} gadi_opts;
+
+typedef struct {
+    int outer_its;          /* outer iterations done (x_k with k = outer_its) */
+    long long inner_its_h;  /* total CG iterations on H                      */
+    long long inner_its_s;  /* total CGNR iterations on S                    */
+    double relres;          /* ||b - A x|| / ||b - A x_0|| at exit (FP64)    */
+    double r0_norm;         /* ||b - A x_0||                                 */
+    double seconds;         /* device time of the solve (CUDA events)        */
+    int status;             /* same as the return value                      */
+    int blocks;             /* persistent blocks launched                    */
+} gadi_stats;
+
+typedef struct gadi_handle gadi_handle;
+
+/* Fill *o with the defaults listed above for precision u_low. */
+void gadi_opts_default(gadi_opts *o, gadi_prec u_low);
+
+/* Human-readable name of a status code (static string). */
+const char *gadi_status_str(gadi_status s);
+
+/* Build the operator set for a problem and a splitting (Sec. 3.1) on the
+ * current CUDA device.  Stencils are matrix-free: only scalars are kept.
+ * CSR: A, M = (A + A^T)/2 and N = (A - A^T)/2 are formed in FP64 on the host
+ * and copied to the device.  Errors: INVALID (sizes <= 0, kind or splitting
+ * unknown, CSR pattern out of range), OOM, CUDA.  *out is NULL on error. */
+gadi_status gadi_create(const gadi_problem *prob, gadi_splitting split, gadi_handle **out);
+
+/* Release the handle and its device memory.  NULL is a no-op. */
+void gadi_destroy(gadi_handle *h);
+
+/* Algorithm 1 (Sec. 2.3) with precisions u = u_r = u_high = FP64 and
+ * u_s = u_low.  b: right-hand side (read only); x: initial guess in,
+ * final iterate out (the paper uses x_0 = 0).  Stops when
+ * ||b - A x_k|| / ||b - A x_0|| <= tol (Sec. 5.1) or after maxit outer
+ * iterations.  alpha > 0 and 0 <= omega < 2 (Lemma 1).  opts NULL = defaults;
+ * stats may be NULL.  The whole iteration runs in one persistent cooperative
+ * kernel; stopping decisions are made on the device.
+ * Errors: INVALID (alpha <= 0, omega outside [0,2), u_high != FP64, tol < 0,
+ * maxit < 0), NONFINITE (NaN/Inf in b, x, alpha, omega), TIMEOUT, CUDA, OOM. */
+gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha, double omega,
+                       gadi_prec u_high, gadi_prec u_low, double tol, int maxit,
+                       const gadi_opts *opts, gadi_stats *stats);
+
+/* y = Op x in FP64 for Op in {A, M, N, A^T} (Sec. 3.1 splitting).  x and y
+ * may be host or device memory; stream as in gadi_opts (NULL = default). */
+gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream);
+
+/* ||A||_2 estimate by `iters` steps of power iteration on A^T A in FP64 on
+ * the device (a lower bound; used for the backward error of eq. (3.2)). */
+gadi_status gadi_norm2_estimate(gadi_handle *h, int iters, double *out, void *stream);
+
+/* ---- single steps of Algorithm 1, for verification of each kernel --------
+ * All vectors here are DEVICE pointers.  Vectors in u_s ("u_s vectors") have
+ * element type double (FP64), float (FP32) or uint16 BF16 bit patterns
+ * (BF16), with the same length as x. */
+
+/* Residual step (Algorithm 1 "r = b - A x" in u_r, fused with the previous
+ * update "x = x + y" in u): x_out = x + y (y == NULL: x_out = x),
+ * r = b - A x_out in FP64, *rnorm = ||r||_2, rs = fl_{u_s}(r).
+ * r_out (nullable) receives r in FP64.  x_out must not alias x. */
+gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b, const double *x,
+                               const void *y, double *x_out, double *r_out, void *rs,
+                               double *rnorm, void *stream);
+
+/* H-solve (Algorithm 1 line 3): CG on (alpha I + M) z = rs in u_s from z = 0,
+ * until ||res|| <= tol ||rs|| (tol = 0: exactly maxit steps), or `stag` steps
+ * without a new minimum (0 = off).  *its receives the iteration count. */
+gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, const void *rs,
+                              void *z, double tol, int maxit, int stag, int *its, void *stream);
+
+/* S-solve (Algorithm 1 line 4): g = fl_{u_s}((2 - omega) alpha z), then CG on
+ * S^T S y = S^T g from y = 0 (t_0 = fl_{u_s}(S^T g)), same stopping rules;
+ * pointwise != 0 with the complex class: y = fl_{u_s}(g / (alpha + i sigma)). */
+gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_prec u_low,
+                              const void *z, void *y, double tol, int maxit, int stag,
+                              int pointwise, int *its, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GADI_H */

@@ -19,8 +19,10 @@
  * Precision model (Sec. 5.1 "GADI-FP32" / "GADI-BF16", Table 1):
  *   u = u_r = FP64 always.  u_s is FP64, FP32, or BF16 storage with FP32
  *   arithmetic.  Every stored inner vector element is rounded to u_s at each
- *   write; matrix-vector products and dot products are carried in the compute
- *   type (double for FP64, float otherwise) and are not themselves stored.
+ *   write: r_s, the CG vectors r, p, z, the CGNR vectors t, p, y, the scaled
+ *   right-hand side g and the intermediate S p of CGNR.  The products H p and
+ *   S^T (S p), consumed where they are formed, and all dot products are
+ *   carried in the compute type (double for FP64, float otherwise).
  *   FP32 arithmetic is C float arithmetic (IEEE binary32, round to nearest
  *   even; build with -ffp-contract=off so no fused multiply-add is formed).
  *   BF16 rounding is written out from its definition: round to nearest, ties
@@ -478,7 +480,8 @@ static int cg_f(const orc_op *op1, const op_f *f1, const orc_op *op2, const op_f
             apply_f(op1, f1, p, q);
             pq = dot_f(m, p, q);
         } else {
-            apply_f(op1, f1, p, u);
+            apply_f(op1, f1, p, u);            /* u = S p, stored: rounded to u_s */
+            for (int i = 0; i < m; i++) u[i] = st_f(prec, u[i]);
             pq = dot_f(m, u, u);
             apply_f(op2, f2, u, q);
         }

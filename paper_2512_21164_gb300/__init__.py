@@ -1,0 +1,246 @@
+"""Python binding of the GB300 GADI library (include/gadi.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+`_build/libgadi.so` (built by `paper_2512_21164_gb300.build`).  Vectors are
+torch tensors (CUDA or CPU) or NumPy arrays (host); their raw pointers are
+handed to the C ABI, which detects host vs device memory itself.  There is no
+CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgadi.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gadi.h")
+
+# enums of gadi.h
+OK, NOT_CONVERGED, STAGNATED, DIVERGED = 0, 1, 2, 3
+ERR_INVALID, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+FP64, FP32, BF16 = 0, 1, 2
+SPLIT_HSS = 0
+STENCIL_2D5, STENCIL_3D7, COMPLEX_2D5, CSR = 0, 1, 2, 3
+OP_A, OP_M, OP_N, OP_AT = 0, 1, 2, 3
+PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+
+
+class GadiError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("h", C.c_double), ("beta", C.c_double * 3), ("kappa", C.c_double),
+                ("sigma", C.c_double), ("n", C.c_int), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol_h", C.c_double), ("tol_s", C.c_double), ("maxit_inner", C.c_int),
+                ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
+                ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
+                ("hist", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("outer_its", C.c_int), ("inner_its_h", C.c_longlong),
+                ("inner_its_s", C.c_longlong), ("relres", C.c_double), ("r0_norm", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int), ("blocks", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def lib():
+    """Load libgadi.so (raises if it has not been built)."""
+    global _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"GADI CUDA library not built: {LIB_PATH} missing "
+                                   "(run paper_2512_21164_gb300.build.build())")
+            L = C.CDLL(LIB_PATH)
+            vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+            L.gadi_opts_default.argtypes = [C.POINTER(Opts), C.c_int]
+            L.gadi_opts_default.restype = None
+            L.gadi_status_str.argtypes = [C.c_int]
+            L.gadi_status_str.restype = C.c_char_p
+            L.gadi_create.argtypes = [C.POINTER(Problem), C.c_int, C.POINTER(vp)]
+            L.gadi_destroy.argtypes = [vp]
+            L.gadi_destroy.restype = None
+            L.gadi_solve.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(Stats)]
+            L.gadi_apply.argtypes = [vp, C.c_int, vp, vp, vp]
+            L.gadi_norm2_estimate.argtypes = [vp, C.c_int, dp, vp]
+            L.gadi_step_residual.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, dp, vp]
+            L.gadi_step_solve_h.argtypes = [vp, C.c_double, C.c_int, vp, vp, C.c_double, C.c_int,
+                                            C.c_int, ip, vp]
+            L.gadi_step_solve_s.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp,
+                                            C.c_double, C.c_int, C.c_int, C.c_int, ip, vp]
+            for f in ("gadi_create", "gadi_solve", "gadi_apply", "gadi_norm2_estimate",
+                      "gadi_step_residual", "gadi_step_solve_h", "gadi_step_solve_s"):
+                getattr(L, f).restype = C.c_int
+            _L = L
+    return _L
+
+
+def status_str(s: int) -> str:
+    return lib().gadi_status_str(int(s)).decode()
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or NumPy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported vector type {type(a)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def default_opts(u_low: int) -> Opts:
+    o = Opts()
+    lib().gadi_opts_default(C.byref(o), u_low)
+    return o
+
+
+class Gadi:
+    """One linear system: a handle of the C ABI (gadi_create / gadi_destroy)."""
+
+    def __init__(self, kind, nx=0, ny=1, nz=1, h=0.0, beta=(0.0, 0.0, 0.0), kappa=0.0,
+                 sigma=0.0, rowptr=None, col=None, val=None):
+        import numpy as np
+        P = Problem()
+        P.kind, P.nx, P.ny, P.nz, P.h = int(kind), int(nx), int(ny), int(nz), float(h)
+        P.beta = (C.c_double * 3)(*[float(b) for b in beta])
+        P.kappa, P.sigma = float(kappa), float(sigma)
+        self._keep = []
+        if kind == CSR:
+            rp = np.ascontiguousarray(rowptr, np.int32)
+            cl = np.ascontiguousarray(col, np.int32)
+            vl = np.ascontiguousarray(val, np.float64)
+            self._keep = [rp, cl, vl]
+            P.n = len(rp) - 1
+            P.rowptr, P.col, P.val = rp.ctypes.data, cl.ctypes.data, vl.ctypes.data
+            self.nvec = P.n
+        else:
+            n = int(nx) * int(ny) * (int(nz) if kind == STENCIL_3D7 else 1)
+            self.nvec = 2 * n if kind == COMPLEX_2D5 else n
+        self.kind = kind
+        h_ = C.c_void_p()
+        st = lib().gadi_create(C.byref(P), SPLIT_HSS, C.byref(h_))
+        if st != OK:
+            raise GadiError(st, "gadi_create")
+        self.h = h_
+
+    @classmethod
+    def from_problem(cls, p):
+        """From a workloads.Problem descriptor."""
+        return cls(p.kind, p.nx, p.ny, p.nz, p.h, p.beta, p.kappa, p.sigma, p.rowptr, p.col, p.val)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gadi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------------
+    def solve(self, b, x, alpha, omega=1.0, u_low=FP32, tol=1e-10, maxit=1000, opts=None,
+              hist=None, stream=None, check=True, **kw):
+        """gadi_solve: x (in/out) <- Algorithm 1 iterate.  Returns (status, stats dict)."""
+        o = default_opts(u_low) if opts is None else opts
+        for k, v in kw.items():
+            setattr(o, k, v)
+        o.stream = _stream(stream)
+        if hist is not None:
+            o.hist = _ptr(hist)
+        s = Stats()
+        st = lib().gadi_solve(self.h, _ptr(b), _ptr(x), float(alpha), float(omega), FP64,
+                              int(u_low), float(tol), int(maxit), C.byref(o), C.byref(s))
+        if check and st < 0:
+            raise GadiError(st, "gadi_solve")
+        return st, s.as_dict()
+
+    def apply(self, op, x, y, stream=None):
+        st = lib().gadi_apply(self.h, int(op), _ptr(x), _ptr(y), _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_apply")
+        return y
+
+    def norm2(self, iters=50, stream=None):
+        out = C.c_double()
+        st = lib().gadi_norm2_estimate(self.h, int(iters), C.byref(out), _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_norm2_estimate")
+        return out.value
+
+    def step_residual(self, u_low, b, x, y, x_out, r_out, rs, stream=None):
+        nrm = C.c_double()
+        st = lib().gadi_step_residual(self.h, int(u_low), _ptr(b), _ptr(x), _ptr(y), _ptr(x_out),
+                                      _ptr(r_out), _ptr(rs), C.byref(nrm), _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_step_residual")
+        return nrm.value
+
+    def step_solve_h(self, alpha, u_low, rs, z, tol, maxit, stag=0, stream=None):
+        its = C.c_int()
+        st = lib().gadi_step_solve_h(self.h, float(alpha), int(u_low), _ptr(rs), _ptr(z),
+                                     float(tol), int(maxit), int(stag), C.byref(its),
+                                     _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_step_solve_h")
+        return its.value
+
+    def step_solve_s(self, alpha, omega, u_low, z, y, tol, maxit, stag=0, pointwise=True,
+                     stream=None):
+        its = C.c_int()
+        st = lib().gadi_step_solve_s(self.h, float(alpha), float(omega), int(u_low), _ptr(z),
+                                     _ptr(y), float(tol), int(maxit), int(stag), int(pointwise),
+                                     C.byref(its), _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_step_solve_s")
+        return its.value
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions include/gadi.h declares."""
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gadi_\w+)\s*\(", src)))

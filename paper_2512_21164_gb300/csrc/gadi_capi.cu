@@ -1,0 +1,845 @@
+// Host side of the C ABI declared in include/gadi.h: handle management,
+// argument validation, the operator coefficients of the HSS splitting
+// (rounded to u_s), workspace, host/device pointer staging and the
+// cooperative launches of the persistent kernel.
+#include "gadi.h"
+#include "gadi_inst.h"
+#include "gadi_params.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace gadi;
+
+namespace {
+
+constexpr int kThreadsHost = 256; // must equal gadi::kThreads
+
+// --------------------------------------------------------------------------
+// host-side rounding of FP64 scalars to the storage precision u_s
+// --------------------------------------------------------------------------
+// BF16: first round to odd at binary32 (take the nearest float, step it one
+// unit toward zero if it rounded away, and mark any inexactness in its last
+// bit), then round to nearest even at 8 significant bits on the bit pattern.
+uint16_t host_f32_to_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float host_bf16_to_f32(uint16_t b)
+{
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+float host_round_odd_f32(double d)
+{
+    if (std::isnan(d) || std::isinf(d)) return (float)d;
+    float f = (float)d;
+    if ((double)f == d) return f;
+    if (std::fabs((double)f) > std::fabs(d)) f = std::nextafter(f, 0.0f);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u |= 1u;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+double round_us(int prec, double v)
+{
+    if (prec == P_FP32) return (double)(float)v;
+    if (prec == P_BF16) return (double)host_bf16_to_f32(host_f32_to_bf16(host_round_odd_f32(v)));
+    return v;
+}
+double round_compute(int prec, double v) { return prec == P_FP64 ? v : (double)(float)v; }
+size_t elem_bytes(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2); }
+size_t compute_bytes(int prec) { return prec == P_FP64 ? 8 : 4; }
+
+struct Stencil {
+    double d, c[6], e;
+};
+
+} // namespace
+
+struct gadi_handle {
+    int kind = 0, nx = 0, ny = 0, nz = 0;
+    long long npts = 0, nelem = 0;
+    double h = 0, beta[3] = {0, 0, 0}, kappa = 0, sigma = 0;
+    Stencil A{}, M{}, N{};
+    int device = 0, nsm = 0;
+    // CSR
+    int nnz = 0, nnzm = 0;
+    int *d_rowptr = nullptr, *d_col = nullptr, *d_mrowptr = nullptr, *d_mcol = nullptr;
+    double *d_aval = nullptr, *d_mval = nullptr, *d_nval = nullptr, *d_atval = nullptr;
+    std::vector<int> h_mrowptr, h_mcol;
+    std::vector<double> h_mval, h_nval;
+    void *d_opval = nullptr; // H, S, S^T values in u_s (3 * nnzm elements)
+    int op_prec = -1;
+    double op_alpha = NAN;
+    // workspace
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
+    double *d_part = nullptr, *d_hist = nullptr;
+    int part_cap = 0, hist_cap = 0;
+    Ctl *d_ctl = nullptr, *h_ctl = nullptr;
+    unsigned long long *d_bar = nullptr;
+    int *d_abort = nullptr, *d_flag = nullptr, *h_flag = nullptr;
+    double *d_stage = nullptr; // 2 * nelem doubles for host b / x
+    double *d_pw = nullptr;    // power-iteration vectors (3 * nelem)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+gadi_status cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? GADI_ERR_OOM : GADI_ERR_CUDA; }
+#define CK(call)                                                                                             \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess) return cuda_err(e_);                                                          \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void stencil_coefs(gadi_handle *h)
+{
+    const double cx = h->beta[0] * h->h / 2.0, cy = h->beta[1] * h->h / 2.0, cz = h->beta[2] * h->h / 2.0;
+    Stencil M{}, N{};
+    if (h->kind == GADI_STENCIL_2D5) {
+        M.d = 4.0;
+        for (int k = 0; k < 4; k++) M.c[k] = -1.0;
+        N.c[0] = -cx; N.c[1] = cx; N.c[2] = -cy; N.c[3] = cy;
+    } else if (h->kind == GADI_STENCIL_3D7) {
+        M.d = 6.0;
+        for (int k = 0; k < 6; k++) M.c[k] = -1.0;
+        N.c[0] = -cx; N.c[1] = cx; N.c[2] = -cy; N.c[3] = cy; N.c[4] = -cz; N.c[5] = cz;
+    } else {
+        M.d = 4.0 + h->kappa;
+        for (int k = 0; k < 4; k++) M.c[k] = -1.0;
+        N.e = h->sigma;
+    }
+    Stencil A{};
+    A.d = M.d + N.d;
+    for (int k = 0; k < 6; k++) A.c[k] = M.c[k] + N.c[k];
+    A.e = M.e + N.e;
+    h->A = A;
+    h->M = M;
+    h->N = N;
+}
+
+gadi_status ensure_ctl(gadi_handle *h, int blocks, int maxit)
+{
+    if (!h->d_ctl) {
+        CK(cudaMalloc(&h->d_ctl, sizeof(Ctl)));
+        CK(cudaMallocHost(&h->h_ctl, sizeof(Ctl)));
+        CK(cudaMalloc(&h->d_bar, 64));
+        CK(cudaMalloc(&h->d_abort, 64));
+        CK(cudaMalloc(&h->d_flag, 64));
+        CK(cudaMallocHost(&h->h_flag, 64));
+        CK(cudaEventCreate(&h->ev0));
+        CK(cudaEventCreate(&h->ev1));
+    }
+    if (blocks > h->part_cap) {
+        if (h->d_part) cudaFree(h->d_part);
+        h->d_part = nullptr;
+        CK(cudaMalloc(&h->d_part, sizeof(double) * 4 * (size_t)blocks));
+        h->part_cap = blocks;
+    }
+    if (maxit + 2 > h->hist_cap) {
+        if (h->d_hist) cudaFree(h->d_hist);
+        h->d_hist = nullptr;
+        CK(cudaMalloc(&h->d_hist, sizeof(double) * (size_t)(maxit + 2)));
+        h->hist_cap = maxit + 2;
+    }
+    return GADI_OK;
+}
+
+// workspace layout: x1 (FP64), then r, z, p0, p1, y, u in u_s, then q in the
+// compute type (CSR only), each slab aligned to 256 bytes
+struct Work {
+    double *x1;
+    void *r, *z, *p0, *p1, *y, *u, *q;
+};
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+gadi_status ensure_ws(gadi_handle *h, int prec, Work *w)
+{
+    const size_t m = (size_t)h->nelem;
+    const size_t sv = align256(m * elem_bytes(prec)), dv = align256(m * 8), cv = align256(m * compute_bytes(prec));
+    const size_t need = dv + 6 * sv + (h->kind == GADI_CSR ? cv : 0);
+    if (need > h->ws_bytes) {
+        if (h->d_ws) cudaFree(h->d_ws);
+        h->d_ws = nullptr;
+        h->ws_bytes = 0;
+        CK(cudaMalloc(&h->d_ws, need));
+        h->ws_bytes = need;
+    }
+    char *b = (char *)h->d_ws;
+    w->x1 = (double *)b;
+    b += dv;
+    void **slots[6] = {&w->r, &w->z, &w->p0, &w->p1, &w->y, &w->u};
+    for (int i = 0; i < 6; i++) {
+        *slots[i] = b;
+        b += sv;
+    }
+    w->q = h->kind == GADI_CSR ? (void *)b : nullptr;
+    return GADI_OK;
+}
+
+template <class T> void to_storage(int prec, const std::vector<double> &v, std::vector<T> &out);
+
+// u_s copies of H = alpha I + M, S = alpha I + N and S^T = alpha I - N on M's
+// pattern (CSR only); the shift is added in FP64 before rounding.
+gadi_status ensure_csr_ops(gadi_handle *h, int prec, double alpha)
+{
+    if (h->op_prec == prec && h->op_alpha == alpha) return GADI_OK;
+    const int n = (int)h->npts, nnz = h->nnzm;
+    std::vector<double> hv(nnz), sv(nnz), tv(nnz);
+    for (int i = 0; i < n; i++)
+        for (int k = h->h_mrowptr[i]; k < h->h_mrowptr[i + 1]; k++) {
+            const double sh = h->h_mcol[k] == i ? alpha : 0.0;
+            hv[k] = round_us(prec, h->h_mval[k] + sh);
+            sv[k] = round_us(prec, h->h_nval[k] + sh);
+            tv[k] = round_us(prec, sh - h->h_nval[k]);
+        }
+    const size_t eb = elem_bytes(prec);
+    std::vector<unsigned char> buf(3 * (size_t)nnz * eb + 16);
+    for (int part = 0; part < 3; part++) {
+        const std::vector<double> &src = part == 0 ? hv : (part == 1 ? sv : tv);
+        unsigned char *dst = buf.data() + (size_t)part * nnz * eb;
+        for (int k = 0; k < nnz; k++) {
+            if (prec == P_FP64) {
+                std::memcpy(dst + 8 * (size_t)k, &src[k], 8);
+            } else if (prec == P_FP32) {
+                float f = (float)src[k];
+                std::memcpy(dst + 4 * (size_t)k, &f, 4);
+            } else {
+                uint16_t b = host_f32_to_bf16((float)src[k]); // exact: already a BF16 value
+                std::memcpy(dst + 2 * (size_t)k, &b, 2);
+            }
+        }
+    }
+    if (h->d_opval) cudaFree(h->d_opval);
+    h->d_opval = nullptr;
+    h->op_prec = -1;
+    CK(cudaMalloc(&h->d_opval, buf.size()));
+    CK(cudaMemcpy(h->d_opval, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    h->op_prec = prec;
+    h->op_alpha = alpha;
+    return GADI_OK;
+}
+
+bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+// Every vector the kernel reads or writes with 16-byte loads must start on a
+// 16-byte boundary; the narrow path needs only the element alignment, except
+// for complex FP64 points (16 bytes), which always need 16.
+bool params_aligned(const Params &P)
+{
+    const void *ps[] = {P.b, P.x, P.x1, P.r_out, P.r, P.z, P.p0, P.p1, P.y, P.u, P.ax_in, P.ax_out};
+    for (const void *p : ps)
+        if (!aligned16(p)) return false;
+    return true;
+}
+
+const void *pick_kernel(gadi_handle *h, int prec, bool aligned)
+{
+    if (h->kind == GADI_CSR) return kernel_csr(prec);
+    const long long ne = (long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1);
+    const int vec = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
+    const int v = aligned && (ne % vec) == 0;
+    if (h->kind == GADI_STENCIL_2D5) return kernel_2d5(prec, v);
+    if (h->kind == GADI_STENCIL_3D7) return kernel_3d7(prec, v);
+    return kernel_c2d5(prec, v);
+}
+
+gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStream_t st, int *blocks_out)
+{
+    const bool al = params_aligned(P);
+    if (!al && h->kind == GADI_COMPLEX_2D5) return GADI_ERR_INVALID; // complex vectors: 16-byte aligned
+    const void *k = pick_kernel(h, prec, al);
+    if (!k) return GADI_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, 0));
+    if (per_sm <= 0) return GADI_ERR_CUDA;
+    int blocks = per_sm * h->nsm;
+    if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
+    gadi_status s = ensure_ctl(h, blocks, std::max(P.maxit, 1));
+    if (s != GADI_OK) return s;
+    P.part = h->d_part;
+    P.hist = h->d_hist;
+    P.ctl = h->d_ctl;
+    P.bar = h->d_bar;
+    P.abort_flag = h->d_abort;
+    CK(cudaMemsetAsync(h->d_bar, 0, 64, st));
+    CK(cudaMemsetAsync(h->d_abort, 0, 64, st));
+    CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st));
+    void *args[] = {&P};
+    CK(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreadsHost), args, 0, st));
+    if (blocks_out) *blocks_out = blocks;
+    return GADI_OK;
+}
+
+// read back the control block and the abort flag; TIMEOUT if a wait gave up
+gadi_status finish(gadi_handle *h, cudaStream_t st)
+{
+    CK(cudaMemcpyAsync(h->h_ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_flag, h->d_abort, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_flag[0]) return GADI_ERR_TIMEOUT;
+    return GADI_OK;
+}
+
+void fill_base(gadi_handle *h, Params &P, int prec)
+{
+    std::memset(&P, 0, sizeof P);
+    P.kind = h->kind;
+    P.prec = prec;
+    P.nx = h->nx;
+    P.ny = h->ny;
+    P.nz = h->nz;
+    P.npts = h->npts;
+    P.nelem = h->nelem;
+    Coefs &c = P.co;
+    c.a_d = h->A.d;
+    c.a_e = h->A.e;
+    for (int k = 0; k < 6; k++) {
+        c.a_c[k] = h->A.c[k];
+        c.m_c[k] = h->M.c[k];
+        c.n_c[k] = h->N.c[k];
+    }
+    c.m_d = h->M.d;
+    c.n_e = h->N.e;
+    if (h->kind == GADI_CSR) {
+        P.rowptr = h->d_rowptr;
+        P.col = h->d_col;
+        P.aval = h->d_aval;
+        P.mrowptr = h->d_mrowptr;
+        P.mcol = h->d_mcol;
+        P.mval_d = h->d_mval;
+        P.nval_d = h->d_nval;
+    }
+}
+
+// inner-solve coefficients for (alpha, omega, prec)
+void fill_inner(gadi_handle *h, Params &P, int prec, double alpha, double omega)
+{
+    Coefs &c = P.co;
+    c.h_d = round_us(prec, alpha + h->M.d);
+    c.s_d = round_us(prec, alpha);
+    c.t_d = c.s_d;
+    for (int k = 0; k < 6; k++) {
+        c.h_c[k] = round_us(prec, h->M.c[k]);
+        c.s_c[k] = round_us(prec, h->N.c[k]);
+        c.t_c[k] = -c.s_c[k];
+    }
+    c.s_e = round_us(prec, h->N.e);
+    c.t_e = -c.s_e;
+    c.gamma = round_compute(prec, (2.0 - omega) * alpha);
+    if (h->kind == GADI_CSR) {
+        const size_t eb = elem_bytes(prec), nn = (size_t)h->nnzm;
+        P.hval = h->d_opval;
+        P.sval = (const char *)h->d_opval + nn * eb;
+        P.tval = (const char *)h->d_opval + 2 * nn * eb;
+    }
+}
+
+__global__ void k_nonfinite(const double *v, long long n, int *flag)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) {
+            atomicExch(flag, 1);
+            return;
+        }
+}
+
+gadi_status check_finite_dev(gadi_handle *h, const double *v, long long n, cudaStream_t st, bool *ok)
+{
+    CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), st));
+    k_nonfinite<<<std::max(1, h->nsm * 4), 256, 0, st>>>(v, n, h->d_flag);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_flag + 1, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *ok = h->h_flag[1] == 0;
+    return GADI_OK;
+}
+
+bool check_finite_host(const double *v, long long n)
+{
+    for (long long i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+__global__ void k_dot(const double *a, const double *b, long long n, double *out)
+{
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s = fma(a[i], b[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+__global__ void k_scale_copy(const double *a, double s, long long n, double *out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] * s;
+}
+__global__ void k_init_pw(double *v, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + 0x1234567ull;
+        z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+        v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) + 0.5;
+    }
+}
+
+gadi_status apply_dev(gadi_handle *h, gadi_op op, const double *x, double *y, cudaStream_t st)
+{
+    Params P;
+    fill_base(h, P, P_FP64);
+    P.mode = MODE_APPLY;
+    P.op = op;
+    P.ax_in = x;
+    P.ax_out = y;
+    P.maxit = 1;
+    if (h->kind == GADI_CSR) {
+        if (op != GADI_OP_A) {
+            P.rowptr = h->d_mrowptr;
+            P.col = h->d_mcol;
+            P.aval = op == GADI_OP_M ? h->d_mval : (op == GADI_OP_N ? h->d_nval : h->d_atval);
+        }
+    } else {
+        const Stencil &M = h->M, &N = h->N;
+        Stencil s{};
+        if (op == GADI_OP_A) s = h->A;
+        else if (op == GADI_OP_M) s = M;
+        else if (op == GADI_OP_N) s = N;
+        else { // transpose of the real (block) form: M - N
+            s.d = M.d - N.d;
+            for (int k = 0; k < 6; k++) s.c[k] = M.c[k] - N.c[k];
+            s.e = M.e - N.e;
+        }
+        P.co.a_d = s.d;
+        P.co.a_e = s.e;
+        for (int k = 0; k < 6; k++) P.co.a_c[k] = s.c[k];
+    }
+    gadi_status r = launch(h, P_FP64, P, 0, st, nullptr);
+    if (r != GADI_OK) return r;
+    return finish(h, st);
+}
+
+gadi_status opts_check(const gadi_opts &o)
+{
+    if (!(o.tol_h >= 0) || !(o.tol_s >= 0) || o.maxit_inner < 0 || o.inner_stag < 0 || o.outer_stag_window < 0)
+        return GADI_ERR_INVALID;
+    return GADI_OK;
+}
+
+} // namespace
+
+// ==========================================================================
+// public API
+// ==========================================================================
+extern "C" {
+
+void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->tol_h = o->tol_s = (u_low == GADI_BF16) ? 1e-2 : 1e-3;
+    o->maxit_inner = 1000;
+    o->inner_stag = 10;
+    o->outer_stag_window = 50;
+    o->s_pointwise = 1;
+    o->stream = nullptr;
+    o->max_blocks = 0;
+    o->hist = nullptr;
+}
+
+const char *gadi_status_str(gadi_status s)
+{
+    switch (s) {
+    case GADI_OK: return "GADI_OK";
+    case GADI_NOT_CONVERGED: return "GADI_NOT_CONVERGED";
+    case GADI_STAGNATED: return "GADI_STAGNATED";
+    case GADI_DIVERGED: return "GADI_DIVERGED";
+    case GADI_ERR_INVALID: return "GADI_ERR_INVALID";
+    case GADI_ERR_NONFINITE: return "GADI_ERR_NONFINITE";
+    case GADI_ERR_CUDA: return "GADI_ERR_CUDA";
+    case GADI_ERR_OOM: return "GADI_ERR_OOM";
+    case GADI_ERR_TIMEOUT: return "GADI_ERR_TIMEOUT";
+    case GADI_ERR_UNSUPPORTED: return "GADI_ERR_UNSUPPORTED";
+    }
+    return "GADI_UNKNOWN_STATUS";
+}
+
+gadi_status gadi_create(const gadi_problem *p, gadi_splitting split, gadi_handle **out)
+{
+    if (!out) return GADI_ERR_INVALID;
+    *out = nullptr;
+    if (!p || split != GADI_SPLIT_HSS) return GADI_ERR_INVALID;
+    if (p->kind < GADI_STENCIL_2D5 || p->kind > GADI_CSR) return GADI_ERR_INVALID;
+    gadi_handle *h = new (std::nothrow) gadi_handle();
+    if (!h) return GADI_ERR_OOM;
+    h->kind = p->kind;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return GADI_ERR_CUDA;
+    }
+    gadi_status st = GADI_OK;
+    if (p->kind != GADI_CSR) {
+        if (p->nx <= 0 || p->ny <= 0 || (p->kind == GADI_STENCIL_3D7 && p->nz <= 0)) st = GADI_ERR_INVALID;
+        for (int k = 0; k < 3; k++)
+            if (!std::isfinite(p->beta[k])) st = GADI_ERR_NONFINITE;
+        if (!std::isfinite(p->kappa) || !std::isfinite(p->sigma) || !std::isfinite(p->h)) st = GADI_ERR_NONFINITE;
+        if (st == GADI_OK) {
+            h->nx = p->nx;
+            h->ny = p->ny;
+            h->nz = p->kind == GADI_STENCIL_3D7 ? p->nz : 1;
+            h->npts = (long long)h->nx * h->ny * h->nz;
+            h->nelem = h->kind == GADI_COMPLEX_2D5 ? 2 * h->npts : h->npts;
+            if ((long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1) > (1ll << 30)) st = GADI_ERR_INVALID;
+            h->h = p->h > 0 ? p->h : 1.0 / (p->nx + 1);
+            for (int k = 0; k < 3; k++) h->beta[k] = p->beta[k];
+            h->kappa = p->kappa;
+            h->sigma = p->sigma;
+            stencil_coefs(h);
+        }
+    } else {
+        const int n = p->n;
+        if (n <= 0 || !p->rowptr || !p->col || !p->val) st = GADI_ERR_INVALID;
+        if (st == GADI_OK && (p->rowptr[0] != 0)) st = GADI_ERR_INVALID;
+        if (st == GADI_OK)
+            for (int i = 0; i < n; i++)
+                if (p->rowptr[i + 1] < p->rowptr[i]) st = GADI_ERR_INVALID;
+        const int nnz = st == GADI_OK ? p->rowptr[n] : 0;
+        if (st == GADI_OK)
+            for (int k = 0; k < nnz; k++) {
+                if (p->col[k] < 0 || p->col[k] >= n) st = GADI_ERR_INVALID;
+                if (!std::isfinite(p->val[k])) st = GADI_ERR_NONFINITE;
+            }
+        if (st == GADI_OK) {
+            h->npts = h->nelem = n;
+            h->nx = n;
+            h->ny = h->nz = 1;
+            h->nnz = nnz;
+            // M = (A + A^T)/2, N = (A - A^T)/2 on the union pattern plus the
+            // diagonal, columns sorted (dense row scatter, one row at a time)
+            std::vector<std::vector<std::pair<int, double>>> at(n);
+            for (int i = 0; i < n; i++)
+                for (int k = p->rowptr[i]; k < p->rowptr[i + 1]; k++) at[p->col[k]].push_back({i, p->val[k]});
+            std::vector<double> ra(n, 0.0), rt(n, 0.0);
+            std::vector<char> mark(n, 0);
+            std::vector<int> cols;
+            h->h_mrowptr.assign(n + 1, 0);
+            for (int i = 0; i < n; i++) {
+                cols.clear();
+                auto touch = [&](int j) {
+                    if (!mark[j]) {
+                        mark[j] = 1;
+                        cols.push_back(j);
+                    }
+                };
+                touch(i);
+                for (int k = p->rowptr[i]; k < p->rowptr[i + 1]; k++) {
+                    touch(p->col[k]);
+                    ra[p->col[k]] += p->val[k];
+                }
+                for (auto &e : at[i]) {
+                    touch(e.first);
+                    rt[e.first] += e.second;
+                }
+                std::sort(cols.begin(), cols.end());
+                for (int j : cols) {
+                    h->h_mcol.push_back(j);
+                    h->h_mval.push_back((ra[j] + rt[j]) * 0.5);
+                    h->h_nval.push_back((ra[j] - rt[j]) * 0.5);
+                    ra[j] = rt[j] = 0.0;
+                    mark[j] = 0;
+                }
+                h->h_mrowptr[i + 1] = (int)h->h_mcol.size();
+            }
+            h->nnzm = (int)h->h_mcol.size();
+            std::vector<double> atv(h->nnzm);
+            for (int k = 0; k < h->nnzm; k++) atv[k] = h->h_mval[k] - h->h_nval[k];
+            auto up = [&](void **d, const void *src, size_t bytes) -> bool {
+                if (cudaMalloc(d, bytes ? bytes : 16) != cudaSuccess) return false;
+                return bytes == 0 || cudaMemcpy(*d, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+            };
+            bool ok = up((void **)&h->d_rowptr, p->rowptr, sizeof(int) * (n + 1)) &&
+                      up((void **)&h->d_col, p->col, sizeof(int) * nnz) &&
+                      up((void **)&h->d_aval, p->val, sizeof(double) * nnz) &&
+                      up((void **)&h->d_mrowptr, h->h_mrowptr.data(), sizeof(int) * (n + 1)) &&
+                      up((void **)&h->d_mcol, h->h_mcol.data(), sizeof(int) * h->nnzm) &&
+                      up((void **)&h->d_mval, h->h_mval.data(), sizeof(double) * h->nnzm) &&
+                      up((void **)&h->d_nval, h->h_nval.data(), sizeof(double) * h->nnzm) &&
+                      up((void **)&h->d_atval, atv.data(), sizeof(double) * h->nnzm);
+            if (!ok) st = GADI_ERR_OOM;
+        }
+    }
+    if (st != GADI_OK) {
+        gadi_destroy(h);
+        return st;
+    }
+    *out = h;
+    return GADI_OK;
+}
+
+void gadi_destroy(gadi_handle *h)
+{
+    if (!h) return;
+    void *dev[] = {h->d_rowptr, h->d_col, h->d_mrowptr, h->d_mcol, h->d_aval, h->d_mval, h->d_nval,
+                   h->d_atval, h->d_opval, h->d_ws, h->d_part, h->d_hist, h->d_ctl, h->d_bar,
+                   h->d_abort, h->d_flag, h->d_stage, h->d_pw};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha, double omega,
+                       gadi_prec u_high, gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
+                       gadi_stats *stats)
+{
+    if (!h || !b || !x) return GADI_ERR_INVALID;
+    if (!std::isfinite(alpha) || !std::isfinite(omega) || std::isnan(tol)) return GADI_ERR_NONFINITE;
+    if (!(alpha > 0) || !(omega >= 0 && omega < 2) || u_high != GADI_FP64 || !(tol >= 0) || maxit < 0)
+        return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    gadi_opts o;
+    if (opts) o = *opts;
+    else gadi_opts_default(&o, u_low);
+    gadi_status s = opts_check(o);
+    if (s != GADI_OK) return s;
+    const int prec = (int)u_low;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const long long m = h->nelem;
+    const size_t vb = sizeof(double) * (size_t)m;
+
+    // stage host vectors
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    if (!bdev || !xdev) {
+        if (!h->d_stage) CK(cudaMalloc(&h->d_stage, 2 * vb));
+    }
+    if (!bdev && !check_finite_host(b, m)) return GADI_ERR_NONFINITE;
+    if (!xdev && !check_finite_host(x, m)) return GADI_ERR_NONFINITE;
+    const double *db = bdev ? b : h->d_stage;
+    double *dx = xdev ? x : h->d_stage + m;
+    if (!bdev) CK(cudaMemcpyAsync((void *)db, b, vb, cudaMemcpyHostToDevice, st));
+    if (!xdev) CK(cudaMemcpyAsync(dx, x, vb, cudaMemcpyHostToDevice, st));
+    if (bdev || xdev) {
+        bool ok = true;
+        if (bdev && (s = check_finite_dev(h, b, m, st, &ok)) != GADI_OK) return s;
+        if (!ok) return GADI_ERR_NONFINITE;
+        if (xdev && (s = check_finite_dev(h, x, m, st, &ok)) != GADI_OK) return s;
+        if (!ok) return GADI_ERR_NONFINITE;
+    }
+
+    Work w;
+    if ((s = ensure_ws(h, prec, &w)) != GADI_OK) return s;
+    if (h->kind == GADI_CSR && (s = ensure_csr_ops(h, prec, alpha)) != GADI_OK) return s;
+    Params P;
+    fill_base(h, P, prec);
+    fill_inner(h, P, prec, alpha, omega);
+    P.mode = MODE_SOLVE;
+    P.b = db;
+    P.x = dx;
+    P.x1 = w.x1;
+    P.r = w.r; P.z = w.z; P.p0 = w.p0; P.p1 = w.p1; P.y = w.y; P.u = w.u; P.q = w.q;
+    P.tol = tol;
+    P.tol_h = o.tol_h;
+    P.tol_s = o.tol_s;
+    P.maxit = maxit;
+    P.maxit_inner = o.maxit_inner;
+    P.inner_stag = o.inner_stag;
+    P.outer_win = o.outer_stag_window;
+    P.pointwise = o.s_pointwise;
+    CK(cudaEventRecord(h->ev0, st));
+    int blocks = 0;
+    if ((s = launch(h, prec, P, o.max_blocks, st, &blocks)) != GADI_OK) return s;
+    CK(cudaEventRecord(h->ev1, st));
+    if ((s = finish(h, st)) != GADI_OK) return s;
+    const Ctl c = *h->h_ctl;
+    if (c.x_in_x1) CK(cudaMemcpyAsync(dx, w.x1, vb, cudaMemcpyDeviceToDevice, st));
+    if (!xdev) CK(cudaMemcpyAsync(x, dx, vb, cudaMemcpyDeviceToHost, st));
+    if (o.hist) CK(cudaMemcpyAsync(o.hist, h->d_hist, sizeof(double) * (size_t)(c.outer_its + 1),
+                                   cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (stats) {
+        stats->outer_its = c.outer_its;
+        stats->inner_its_h = c.inner_h;
+        stats->inner_its_s = c.inner_s;
+        stats->relres = c.relres;
+        stats->r0_norm = c.r0;
+        stats->seconds = ms * 1e-3;
+        stats->status = c.status;
+        stats->blocks = blocks;
+    }
+    return (gadi_status)c.status;
+}
+
+gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream)
+{
+    if (!h || !x || !y || op < GADI_OP_A || op > GADI_OP_AT || x == y) return GADI_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = sizeof(double) * (size_t)h->nelem;
+    const bool xd = is_device_ptr(x), yd = is_device_ptr(y);
+    if (!xd || !yd)
+        if (!h->d_stage) CK(cudaMalloc(&h->d_stage, 2 * vb));
+    const double *dx = xd ? x : h->d_stage;
+    double *dy = yd ? y : h->d_stage + h->nelem;
+    if (!xd) CK(cudaMemcpyAsync((void *)dx, x, vb, cudaMemcpyHostToDevice, st));
+    gadi_status s = apply_dev(h, op, dx, dy, st);
+    if (s != GADI_OK) return s;
+    if (!yd) {
+        CK(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return GADI_OK;
+}
+
+gadi_status gadi_norm2_estimate(gadi_handle *h, int iters, double *out, void *stream)
+{
+    if (!h || !out || iters <= 0) return GADI_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long m = h->nelem;
+    if (!h->d_pw) CK(cudaMalloc(&h->d_pw, sizeof(double) * (3 * (size_t)m + 2)));
+    double *v = h->d_pw, *t = v + m, *wv = t + m, *acc = wv + m;
+    const int gb = std::max(1, h->nsm * 4);
+    k_init_pw<<<gb, 256, 0, st>>>(v, m);
+    CK(cudaGetLastError());
+    double hs = 0.0;
+    for (int it = 0; it < iters + 1; it++) {
+        // v <- v / ||v||
+        CK(cudaMemsetAsync(acc, 0, sizeof(double), st));
+        k_dot<<<gb, 256, 0, st>>>(v, v, m, acc);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&hs, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (!(hs > 0)) {
+            *out = 0.0;
+            return GADI_OK;
+        }
+        if (it == iters) break;
+        k_scale_copy<<<gb, 256, 0, st>>>(v, 1.0 / std::sqrt(hs), m, v);
+        gadi_status s = apply_dev(h, GADI_OP_A, v, t, st);
+        if (s != GADI_OK) return s;
+        if ((s = apply_dev(h, GADI_OP_AT, t, wv, st)) != GADI_OK) return s;
+        std::swap(v, wv);
+    }
+    // after the loop ||v|| = ||A^T A v_prev|| with ||v_prev|| = 1
+    *out = std::sqrt(std::sqrt(hs));
+    return GADI_OK;
+}
+
+gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b, const double *x,
+                               const void *y, double *x_out, double *r_out, void *rs, double *rnorm,
+                               void *stream)
+{
+    if (!h || !b || !x || !x_out || !rs || x_out == x) return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    const int prec = (int)u_low;
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    gadi_status s = ensure_ws(h, prec, &w);
+    if (s != GADI_OK) return s;
+    Params P;
+    fill_base(h, P, prec);
+    P.mode = MODE_RESIDUAL;
+    P.b = b;
+    P.x = (double *)x;
+    P.y = (void *)y;
+    P.x1 = x_out;
+    P.r_out = r_out;
+    P.r = rs;
+    P.maxit = 1;
+    if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;
+    if ((s = finish(h, st)) != GADI_OK) return s;
+    if (rnorm) *rnorm = h->h_ctl->rnorm;
+    return GADI_OK;
+}
+
+gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, const void *rs, void *z,
+                              double tol, int maxit, int stag, int *its, void *stream)
+{
+    if (!h || !rs || !z || !(alpha > 0) || !(tol >= 0) || maxit < 0 || stag < 0) return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    const int prec = (int)u_low;
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    gadi_status s = ensure_ws(h, prec, &w);
+    if (s != GADI_OK) return s;
+    if (h->kind == GADI_CSR && (s = ensure_csr_ops(h, prec, alpha)) != GADI_OK) return s;
+    CK(cudaMemcpyAsync(w.r, rs, elem_bytes(prec) * (size_t)h->nelem, cudaMemcpyDeviceToDevice, st));
+    Params P;
+    fill_base(h, P, prec);
+    fill_inner(h, P, prec, alpha, 1.0);
+    P.mode = MODE_SOLVE_H;
+    P.r = w.r; P.z = z; P.p0 = w.p0; P.p1 = w.p1; P.q = w.q;
+    P.tol_h = tol;
+    P.maxit_inner = maxit;
+    P.inner_stag = stag;
+    P.maxit = 1;
+    if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;
+    if ((s = finish(h, st)) != GADI_OK) return s;
+    if (its) *its = (int)h->h_ctl->inner_h;
+    return GADI_OK;
+}
+
+gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_prec u_low, const void *z,
+                              void *y, double tol, int maxit, int stag, int pointwise, int *its,
+                              void *stream)
+{
+    if (!h || !z || !y || !(alpha > 0) || !(omega >= 0 && omega < 2) || !(tol >= 0) || maxit < 0 || stag < 0)
+        return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    const int prec = (int)u_low;
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    gadi_status s = ensure_ws(h, prec, &w);
+    if (s != GADI_OK) return s;
+    if (h->kind == GADI_CSR && (s = ensure_csr_ops(h, prec, alpha)) != GADI_OK) return s;
+    Params P;
+    fill_base(h, P, prec);
+    fill_inner(h, P, prec, alpha, omega);
+    P.mode = MODE_SOLVE_S;
+    P.z = (void *)z; P.y = y; P.r = w.r; P.u = w.u; P.p0 = w.p0; P.p1 = w.p1; P.q = w.q;
+    P.tol_s = tol;
+    P.maxit_inner = maxit;
+    P.inner_stag = stag;
+    P.pointwise = pointwise;
+    P.maxit = 1;
+    if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;
+    if ((s = finish(h, st)) != GADI_OK) return s;
+    if (its) *its = (int)h->h_ctl->inner_s;
+    return GADI_OK;
+}
+
+} // extern "C"

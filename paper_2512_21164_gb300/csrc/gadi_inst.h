@@ -1,0 +1,10 @@
+// Kernel lookup across the per-class translation units.
+#pragma once
+namespace gadi {
+// vec = 1 selects the 16-byte vector path (requires the row length in
+// elements to be a multiple of the elements per 16 bytes), 0 the narrow path.
+const void *kernel_2d5(int prec, int vec);
+const void *kernel_3d7(int prec, int vec);
+const void *kernel_c2d5(int prec, int vec);
+const void *kernel_csr(int prec);
+} // namespace gadi

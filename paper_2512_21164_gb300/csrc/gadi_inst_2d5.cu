@@ -1,0 +1,21 @@
+// Instantiations of the persistent GADI kernel for the K_2D5 class.
+#include "gadi_inst.h"
+#include "gadi_solver.cuh"
+
+namespace gadi {
+const void *kernel_2d5(int prec, int vec)
+{
+    switch (prec) {
+    case P_FP64:
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 2, 2>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 1, 1>;
+    case P_FP32:
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 1, 1>;
+    case P_BF16:
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 1, 1>;
+    }
+    return nullptr;
+}
+} // namespace gadi

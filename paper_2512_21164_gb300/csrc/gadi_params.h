@@ -1,0 +1,68 @@
+// Kernel parameter block shared by the host driver and the device code.
+#pragma once
+#include <cstdint>
+
+namespace gadi {
+
+enum : int { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
+enum : int { K_2D5 = 0, K_3D7 = 1, K_C2D5 = 2, K_CSR = 3 };
+
+enum : int {
+    MODE_SOLVE = 0,    // Algorithm 1, all outer iterations
+    MODE_RESIDUAL = 1, // one residual step
+    MODE_SOLVE_H = 2,  // one H-solve (CG)
+    MODE_SOLVE_S = 3,  // one S-solve (CGNR or pointwise)
+    MODE_APPLY = 4     // y = Op x in FP64
+};
+
+// Device-written results of a launch.
+struct Ctl {
+    int status;
+    int outer_its;
+    long long inner_h, inner_s;
+    double relres, r0, rnorm;
+    int x_in_x1;   // 1 if the final iterate sits in the x1 work buffer
+    int pad;
+};
+
+// Operator coefficients.  A is FP64.  H, S and S^T hold values already rounded
+// to u_s on the host (exactly representable in the compute type).
+struct Coefs {
+    double a_d, a_c[6], a_e;
+    double h_d, h_c[6];
+    double s_d, s_c[6], s_e;
+    double t_d, t_c[6], t_e; // S^T (S^H for the complex class)
+    double gamma;            // (2 - omega) alpha, rounded to the compute type
+    double m_d, m_c[6];      // M in FP64 (for gadi_apply)
+    double n_c[6], n_e;      // N in FP64 (for gadi_apply)
+};
+
+struct Params {
+    int kind, prec, mode, op; // op: gadi_op for MODE_APPLY
+    int nx, ny, nz;
+    long long npts, nelem; // nelem = doubles per outer vector
+    Coefs co;
+    // CSR (device arrays)
+    const int *rowptr, *col;
+    const double *aval;                 // A
+    const int *mrowptr, *mcol;          // pattern of M (with full diagonal)
+    const double *mval_d, *nval_d;      // M, N in FP64
+    const void *hval, *sval, *tval;     // H, S, S^T in u_s on M's pattern
+    // vectors
+    const double *b;
+    double *x, *x1, *r_out;
+    void *r, *z, *p0, *p1, *y, *u; // u_s storage
+    void *q;                       // compute type (CSR only)
+    const double *ax_in;           // MODE_APPLY input
+    double *ax_out;                // MODE_APPLY output
+    // control
+    double tol, tol_h, tol_s;
+    int maxit, maxit_inner, inner_stag, outer_win, pointwise, first_y_null;
+    double *part;  // 2 slots x 2 values x gridDim doubles
+    double *hist;  // maxit + 1 doubles (device)
+    Ctl *ctl;
+    unsigned long long *bar;
+    int *abort_flag;
+};
+
+} // namespace gadi

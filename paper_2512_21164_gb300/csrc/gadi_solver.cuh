@@ -1,0 +1,469 @@
+// Algorithm 1 control loop (shared by every operator class) and the CSR
+// implementation of the phase interface.
+#pragma once
+#include "gadi_kernel.cuh"
+
+namespace gadi {
+
+// ---------------------------------------------------------------------------
+// elementwise helpers shared by all classes
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ void phase_norm2(const void *v, long long m, double (&acc)[2])
+{
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using AT = typename AccT<PREC>::T;
+    const S *s = (const S *)v;
+    AT a = AT(0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x) {
+        const AT x = (AT)PT::ld(s[i]);
+        a += x * x;
+    }
+    acc[0] = (double)a;
+    acc[1] = 0.0;
+}
+
+template <int PREC>
+__device__ void phase_zero(void *v, long long m)
+{
+    using S = typename Prec<PREC>::S;
+    S *s = (S *)v;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        s[i] = S(0);
+}
+
+// ---------------------------------------------------------------------------
+// CSR implementation: one thread per row, grid-stride.  Gathers need the
+// whole input vector, so phases that gather from a vector written in the same
+// phase split at an internal grid barrier.
+// ---------------------------------------------------------------------------
+template <int PREC>
+struct CsrImpl {
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    using AT = typename AccT<PREC>::T;
+    static constexpr int K = 1;
+    const Params &P;
+    int n;
+    __device__ explicit CsrImpl(const Params &p) : P(p) { n = (int)p.npts; }
+
+    __device__ long long i0() const { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ long long di() const { return (long long)gridDim.x * blockDim.x; }
+
+    template <class VT, class XT, class AR>
+    __device__ VT spmv_row(const int *rp, const int *cl, const VT *val, const XT *x, int i) const
+    {
+        VT s = VT(0);
+        for (int k = rp[i]; k < rp[i + 1]; k++) s = AR::madd(val[k], (VT)ldx(x, cl[k]), s);
+        return s;
+    }
+    template <class T> __device__ static auto ldx(const T *x, int j)
+    {
+        if constexpr (sizeof(T) == 8) return __ldcg(x + j);
+        else return PT::ld(x[j]);
+    }
+
+    __device__ bool residual(const double *xin, const S *y, double *xout, double (&acc)[2],
+                             const GridSync &gs) const
+    {
+        for (long long i = i0(); i < n; i += di())
+            xout[i] = y ? __dadd_rn(xin[i], PT::to_f64(y[i])) : xin[i];
+        if (!gs.sync()) return false;
+        double a0 = 0.0, a1 = 0.0;
+        S *rs = (S *)P.r;
+        for (long long i = i0(); i < n; i += di()) {
+            const double ax = spmv_row<double, double, ArExact<double>>(P.rowptr, P.col, P.aval, xout, (int)i);
+            const double r = __dsub_rn(P.b[i], ax);
+            a0 = fma(r, r, a0);
+            const S sv = PT::from_f64(r);
+            rs[i] = sv;
+            const double d = PT::to_f64(sv);
+            a1 = fma(d, d, a1);
+            if (P.r_out) P.r_out[i] = r;
+        }
+        acc[0] = a0;
+        acc[1] = a1;
+        return true;
+    }
+    __device__ bool apply(const double *x, double *yout, const GridSync &) const
+    {
+        // op selection is done on the host by pointing rowptr/col/aval at
+        // the operator to apply
+        for (long long i = i0(); i < n; i += di())
+            yout[i] = spmv_row<double, double, ArExact<double>>(P.rowptr, P.col, P.aval, x, (int)i);
+        return true;
+    }
+    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &gs) const
+    {
+        const S *r = (const S *)P.r;
+        for (long long i = i0(); i < n; i += di()) {
+            C v = PT::ld(r[i]);
+            if (!first) v = A::madd(beta, PT::ld(pold[i]), v);
+            pnew[i] = PT::st(v);
+        }
+        if (!gs.sync()) return false;
+        AT a = AT(0);
+        C *q = (C *)P.q;
+        const S *hv = (const S *)P.hval;
+        for (long long i = i0(); i < n; i += di()) {
+            C s = C(0);
+            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
+                s = A::madd(PT::ld(hv[k]), PT::ld(pnew[P.mcol[k]]), s);
+            q[i] = s;
+            a += (AT)PT::ld(pnew[i]) * (AT)s;
+        }
+        acc[0] = (double)a;
+        acc[1] = 0.0;
+        return true;
+    }
+    __device__ bool h2(bool first, C a_, const S *p, double (&acc)[2], const GridSync &) const
+    {
+        S *z = (S *)P.z, *r = (S *)P.r;
+        const C *q = (const C *)P.q;
+        AT a = AT(0);
+        for (long long i = i0(); i < n; i += di()) {
+            const C pp = PT::ld(p[i]);
+            z[i] = PT::st(first ? A::mul(a_, pp) : A::madd(a_, pp, PT::ld(z[i])));
+            const S rn = PT::st(A::madd(-a_, q[i], PT::ld(r[i])));
+            r[i] = rn;
+            const AT rr = (AT)PT::ld(rn);
+            a += rr * rr;
+        }
+        acc[0] = (double)a;
+        acc[1] = 0.0;
+        return true;
+    }
+    __device__ bool s0(C gamma, double (&acc)[2], const GridSync &gs) const
+    {
+        const S *z = (const S *)P.z;
+        S *g = (S *)P.u;
+        for (long long i = i0(); i < n; i += di()) g[i] = PT::st(A::mul(gamma, PT::ld(z[i])));
+        if (!gs.sync()) return false;
+        S *t = (S *)P.r;
+        const S *tv = (const S *)P.tval;
+        AT a = AT(0);
+        for (long long i = i0(); i < n; i += di()) {
+            C s = C(0);
+            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
+                s = A::madd(PT::ld(tv[k]), PT::ld(g[P.mcol[k]]), s);
+            const S ts = PT::st(s);
+            t[i] = ts;
+            const AT x = (AT)PT::ld(ts);
+            a += x * x;
+        }
+        acc[0] = (double)a;
+        acc[1] = 0.0;
+        return true;
+    }
+    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &gs) const
+    {
+        const S *t = (const S *)P.r;
+        for (long long i = i0(); i < n; i += di()) {
+            C v = PT::ld(t[i]);
+            if (!first) v = A::madd(beta, PT::ld(pold[i]), v);
+            pnew[i] = PT::st(v);
+        }
+        if (!gs.sync()) return false;
+        S *u = (S *)P.u;
+        const S *sv = (const S *)P.sval;
+        AT a = AT(0);
+        for (long long i = i0(); i < n; i += di()) {
+            C s = C(0);
+            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
+                s = A::madd(PT::ld(sv[k]), PT::ld(pnew[P.mcol[k]]), s);
+            const S us = PT::st(s);
+            u[i] = us;
+            const AT x = (AT)PT::ld(us);
+            a += x * x;
+        }
+        acc[0] = (double)a;
+        acc[1] = 0.0;
+        return true;
+    }
+    __device__ bool s2(bool first, C a_, const S *p, double (&acc)[2], const GridSync &) const
+    {
+        const S *u = (const S *)P.u;
+        const S *tv = (const S *)P.tval;
+        S *y = (S *)P.y, *t = (S *)P.r;
+        AT a = AT(0);
+        for (long long i = i0(); i < n; i += di()) {
+            C w = C(0);
+            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
+                w = A::madd(PT::ld(tv[k]), PT::ld(u[P.mcol[k]]), w);
+            const C pp = PT::ld(p[i]);
+            y[i] = PT::st(first ? A::mul(a_, pp) : A::madd(a_, pp, PT::ld(y[i])));
+            const S tn = PT::st(A::madd(-a_, w, PT::ld(t[i])));
+            t[i] = tn;
+            const AT x = (AT)PT::ld(tn);
+            a += x * x;
+        }
+        acc[0] = (double)a;
+        acc[1] = 0.0;
+        return true;
+    }
+    __device__ void s_pointwise(C) const {}
+};
+
+// Adapter giving the stencil implementation the same (bool-returning,
+// barrier-taking) interface as the CSR one.
+template <class SI>
+struct StencilAdapter {
+    using S = typename SI::S;
+    using C = typename SI::C;
+    using A = typename SI::A;
+    static constexpr int K = SI::K;
+    SI si;
+    __device__ explicit StencilAdapter(const Params &p) : si(p) {}
+    __device__ bool residual(const double *xin, const S *y, double *xout, double (&acc)[2],
+                             const GridSync &) const
+    {
+        si.residual(xin, y, xout, acc);
+        return true;
+    }
+    __device__ bool apply(const double *x, double *yout, const GridSync &) const
+    {
+        si.apply(x, yout);
+        return true;
+    }
+    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &) const
+    {
+        si.h1(first, beta, pold, pnew, acc);
+        return true;
+    }
+    __device__ bool h2(bool first, C a, const S *p, double (&acc)[2], const GridSync &) const
+    {
+        si.h2(first, a, p, acc);
+        return true;
+    }
+    __device__ bool s0(C gamma, double (&acc)[2], const GridSync &) const
+    {
+        si.s0(gamma, acc);
+        return true;
+    }
+    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &) const
+    {
+        si.s1(first, beta, pold, pnew, acc);
+        return true;
+    }
+    __device__ bool s2(bool first, C a, const S *p, double (&acc)[2], const GridSync &) const
+    {
+        si.s2(first, a, p, acc);
+        return true;
+    }
+    __device__ void s_pointwise(C gamma) const { si.s_pointwise(gamma); }
+};
+
+// ---------------------------------------------------------------------------
+// the control loop
+// ---------------------------------------------------------------------------
+template <int PREC, class Impl>
+struct Runner {
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    const Params &P;
+    const Impl &I;
+    GridSync gs;
+    int slot = 0;
+    double sums[2];
+
+    __device__ Runner(const Params &p, const Impl &i) : P(p), I(i)
+    {
+        gs.counter = p.bar;
+        gs.abort_flag = p.abort_flag;
+        gs.nblocks = gridDim.x;
+    }
+
+    __device__ bool reduce(double (&acc)[2])
+    {
+        const int G = gridDim.x;
+        double *part = P.part + (size_t)slot * 2 * G;
+        block_partials_write<2>(acc, part, G);
+        if (!gs.sync()) return false;
+        grid_partials_sum<2>(part, G, sums);
+        slot ^= 1;
+        return true;
+    }
+
+    // CG on H = alpha I + M (right-hand side already in P.r, ||rhs||^2 = rr0d).
+    // Returns iterations, or -1 if a barrier gave up.
+    __device__ int h_loop(double rr0d)
+    {
+        const long long m = P.nelem;
+        C rr = (C)rr0d;
+        if (rr == C(0)) {
+            phase_zero<PREC>(P.z, m);
+            return gs.sync() ? 0 : -1;
+        }
+        const double thr = P.tol_h * P.tol_h * (double)rr;
+        C beta = C(0), best = rr;
+        int since = 0, its = 0;
+        double acc[2];
+        for (int j = 0; j < P.maxit_inner; ++j) {
+            S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
+            const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
+            if (!I.h1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc)) return -1;
+            const C a = A::div(rr, (C)sums[0]);
+            if (!I.h2(j == 0, a, pnew, acc, gs) || !reduce(acc)) return -1;
+            const C rn = (C)sums[0];
+            its = j + 1;
+            if ((double)rn <= thr) break;
+            if (!(rn == rn)) break;
+            if (rn < best) {
+                best = rn;
+                since = 0;
+            } else if (P.inner_stag > 0 && ++since >= P.inner_stag) {
+                break;
+            }
+            beta = A::div(rn, rr);
+            rr = rn;
+        }
+        return its;
+    }
+
+    // S-solve from z (P.z) into y (P.y).  Returns iterations or -1.
+    __device__ int s_loop(C gamma)
+    {
+        const long long m = P.nelem;
+        if (Impl::K == 2 && P.pointwise) {
+            I.s_pointwise(gamma);
+            return gs.sync() ? 1 : -1;
+        }
+        double acc[2];
+        if (!I.s0(gamma, acc, gs) || !reduce(acc)) return -1;
+        C tt = (C)sums[0];
+        if (tt == C(0)) {
+            phase_zero<PREC>(P.y, m);
+            return gs.sync() ? 0 : -1;
+        }
+        const double thr = P.tol_s * P.tol_s * (double)tt;
+        C beta = C(0), best = tt;
+        int since = 0, its = 0;
+        for (int j = 0; j < P.maxit_inner; ++j) {
+            S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
+            const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
+            if (!I.s1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc)) return -1;
+            const C a = A::div(tt, (C)sums[0]);
+            if (!I.s2(j == 0, a, pnew, acc, gs) || !reduce(acc)) return -1;
+            const C tn = (C)sums[0];
+            its = j + 1;
+            if ((double)tn <= thr) break;
+            if (!(tn == tn)) break;
+            if (tn < best) {
+                best = tn;
+                since = 0;
+            } else if (P.inner_stag > 0 && ++since >= P.inner_stag) {
+                break;
+            }
+            beta = A::div(tn, tt);
+            tt = tn;
+        }
+        return its;
+    }
+
+    __device__ void run()
+    {
+        const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+        double acc[2];
+        if (P.mode == MODE_APPLY) {
+            I.apply(P.ax_in, P.ax_out, gs);
+            return;
+        }
+        if (P.mode == MODE_RESIDUAL) {
+            if (!I.residual(P.x, (const S *)P.y, P.x1, acc, gs) || !reduce(acc)) return;
+            if (leader) {
+                P.ctl->rnorm = sqrt(sums[0]);
+                P.ctl->status = ST_OK;
+            }
+            return;
+        }
+        if (P.mode == MODE_SOLVE_H) {
+            phase_norm2<PREC>(P.r, P.nelem, acc);
+            if (!reduce(acc)) return;
+            const int its = h_loop(sums[0]);
+            if (leader && its >= 0) {
+                P.ctl->inner_h = its;
+                P.ctl->status = ST_OK;
+            }
+            return;
+        }
+        if (P.mode == MODE_SOLVE_S) {
+            const int its = s_loop((C)P.co.gamma);
+            if (leader && its >= 0) {
+                P.ctl->inner_s = its;
+                P.ctl->status = ST_OK;
+            }
+            return;
+        }
+        // MODE_SOLVE: Algorithm 1
+        double r0 = 0.0, rel = 0.0;
+        long long ih = 0, is = 0;
+        int status = ST_NOT_CONVERGED, k = 0, xb = 0;
+        const C gamma = (C)P.co.gamma;
+        for (k = 0;; ++k) {
+            const double *xin = xb ? P.x1 : P.x;
+            double *xout = xb ? P.x : P.x1;
+            if (!I.residual(xin, k > 0 ? (const S *)P.y : nullptr, xout, acc, gs) || !reduce(acc)) return;
+            xb ^= 1;
+            const double rn = sqrt(sums[0]);
+            if (k == 0) r0 = rn;
+            rel = r0 > 0.0 ? rn / r0 : 0.0;
+            if (leader) P.hist[k] = rel;
+            if (rel <= P.tol) {
+                status = ST_OK;
+                break;
+            }
+            if (!(rel == rel) || isinf(rel) || rel > 1e6) {
+                status = ST_DIVERGED;
+                break;
+            }
+            if (P.outer_win > 0 && k >= P.outer_win && rel > 0.99 * __ldcg(P.hist + (k - P.outer_win))) {
+                status = ST_STAGNATED;
+                break;
+            }
+            if (k >= P.maxit) {
+                status = ST_NOT_CONVERGED;
+                break;
+            }
+            const int a = h_loop(sums[1]);
+            if (a < 0) return;
+            ih += a;
+            const int b = s_loop(gamma);
+            if (b < 0) return;
+            is += b;
+        }
+        if (leader) {
+            P.ctl->status = status;
+            P.ctl->outer_its = k;
+            P.ctl->inner_h = ih;
+            P.ctl->inner_s = is;
+            P.ctl->relres = rel;
+            P.ctl->r0 = r0;
+            P.ctl->x_in_x1 = xb;
+        }
+    }
+};
+
+template <int KIND, int PREC, int WI, int WR>
+__global__ void __launch_bounds__(kThreads) gadi_stencil_kernel(const __grid_constant__ Params P)
+{
+    StencilAdapter<StencilImpl<KIND, PREC, WI, WR>> I(P);
+    Runner<PREC, StencilAdapter<StencilImpl<KIND, PREC, WI, WR>>> R(P, I);
+    R.run();
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) gadi_csr_kernel(const __grid_constant__ Params P)
+{
+    CsrImpl<PREC> I(P);
+    Runner<PREC, CsrImpl<PREC>> R(P, I);
+    R.run();
+}
+
+} // namespace gadi

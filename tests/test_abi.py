@@ -1,0 +1,47 @@
+"""The C-ABI library builds, loads and exports every symbol include/gadi.h
+declares; host-only entry points answer without a GPU."""
+import subprocess
+
+import paper_2512_21164_gb300 as G
+from paper_2512_21164_gb300 import build as B
+
+
+def test_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    L = G.lib()
+    declared = G.header_functions()
+    assert "gadi_create" in declared and "gadi_solve" in declared and "gadi_destroy" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("gadi_")}
+    assert set(declared) <= exported
+
+
+def test_status_strings_and_defaults():
+    assert G.status_str(G.OK) == "GADI_OK"
+    assert G.status_str(G.ERR_TIMEOUT) == "GADI_ERR_TIMEOUT"
+    o = G.default_opts(G.BF16)
+    assert o.tol_h == 1e-2 and o.maxit_inner == 1000 and o.s_pointwise == 1
+    o = G.default_opts(G.FP32)
+    assert o.tol_h == 1e-3 and o.outer_stag_window == 50
+
+
+def test_oracle_and_library_share_no_code():
+    """The product package and the oracle are independent: neither imports
+    the other and they share no source file."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2512_21164_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dp, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+                assert "gadi_oracle" not in src, f
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith((".py", ".c")):
+            src = open(os.path.join(root, "oracle", f)).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_2512_21164_gb300\b", src, re.M), f
+            assert "libgadi" not in src, f

@@ -1,0 +1,164 @@
+"""Whole solves (Algorithm 1) on the GPU against the CPU oracle.
+
+Acceptance: the GPU reaches the oracle's outcome (relative residual and
+normwise backward error <= 1e-10 when the oracle does), its forward error is
+within 10x the oracle's, and its outer iteration count is within +-5% (FP64
+inner), +-10% (FP32) or +-25% (BF16) of the oracle's.  Also: the 64 x 64
+plain-FP64 run of 500 iterations, host-pointer and device-pointer calls
+agreeing bit for bit, run-to-run determinism, argument validation and the
+||A||_2 estimate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2512_21164_gb300 as G
+from helpers import BF16, FP32, FP64, dev64
+from workloads import alpha_star, complex_rd, config1, conv_diff_2d, conv_diff_3d, random_csr
+
+pytestmark = pytest.mark.gpu
+
+BAND = {FP64: 0.05, FP32: 0.10, BF16: 0.25}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2512_21164_gb300 import build
+    build.build()
+
+
+def _tols(prec):
+    return (1e-2, 1e-2) if prec == BF16 else (1e-3, 1e-3)
+
+
+def _gpu_solve(p, b, alpha, omega, prec, tol, maxit, **kw):
+    import torch
+    x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+    hist = np.zeros(maxit + 2)
+    th, ts = _tols(prec)
+    with G.Gadi.from_problem(p) as H:
+        st, stats = H.solve(dev64(b), x, alpha, omega, prec, tol, maxit, hist=hist, tol_h=th,
+                            tol_s=ts, **kw)
+    return st, stats, x.cpu().numpy(), hist[:stats["outer_its"] + 1]
+
+
+def _cases():
+    out = []
+    for prec in (FP64, FP32, BF16):
+        p, xt = conv_diff_2d(48, 201, ny=40)
+        out.append(("2d", p, xt, 2 * alpha_star(p), 1.0, prec))
+        p, xt = conv_diff_3d(12, 202)
+        out.append(("3d", p, xt, 2 * alpha_star(p), 1.0, prec))
+        p, xt = complex_rd(24, 203)
+        out.append(("cplx", p, xt, alpha_star(p), 1.0, prec))
+        p, xt = random_csr(400, 204)
+        out.append(("csr", p, xt, 1.0, 1.0, prec))
+    return out
+
+
+@pytest.mark.parametrize("name,p,xt,alpha,omega,prec", _cases(),
+                         ids=[f"{c[0]}-{c[5]}" for c in _cases()])
+def test_solve_matches_oracle(name, p, xt, alpha, omega, prec):
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, alpha, omega, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts,
+                      s_pointwise=True)
+    st, sg, xg, hg = _gpu_solve(p, b, alpha, omega, prec, 1e-10, 3000)
+    assert so["status"] == "OK"
+    assert st == G.OK, G.status_str(st)
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"]), \
+        (sg["outer_its"], so["outer_its"])
+    # FP64 residual and backward error of the GPU iterate, by the oracle
+    r = b - orc.apply(O.OP_A, xg)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1e-10 and abs(rel - sg["relres"]) <= 1e-3 * rel
+    Anorm = O.norm2_power(lambda v: orc.apply(O.OP_A, v),
+                          lambda v: orc.apply(O.OP_M, v) - orc.apply(O.OP_N, v), p.nvec, iters=30)
+    assert O.backward_error(np.linalg.norm(r), Anorm, xg, b) <= 1e-10
+    fe_g = np.linalg.norm(xg - xt) / np.linalg.norm(xt)
+    fe_o = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+    assert fe_g <= 10 * fe_o + 1e-14, (fe_g, fe_o)
+    # the relres histories follow the same trajectory
+    k = min(len(hg), len(so["history"]))
+    ratio = np.abs(np.log10(hg[1:k] / so["history"][1:k]))
+    assert np.median(ratio) < 0.3
+
+
+def test_config1_plain_fp64_500_iterations():
+    """64 x 64, beta=(10,10), alpha=0.5, omega=1, maxit 500, plain FP64: the
+    run ends at the cap (relres ~6e-9) on both sides."""
+    p, xt, c = config1()
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    xo, so = orc.gadi(b, c["alpha"], c["omega"], FP64, tol=c["tol"], maxit=c["maxit"])
+    st, sg, xg, hg = _gpu_solve(p, b, c["alpha"], c["omega"], FP64, c["tol"], c["maxit"])
+    assert so["status"] == "NOT_CONVERGED" and st == G.NOT_CONVERGED
+    assert sg["outer_its"] == so["outer_its"] == 500
+    assert abs(math.log10(sg["relres"] / so["relres"])) < 0.05
+    assert np.allclose(hg, so["history"], rtol=1e-2, atol=0)
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_host_and_device_pointers_agree_and_deterministic():
+    import torch
+    p, xt = conv_diff_2d(40, 205)
+    b = O.Oracle(p).rhs(xt)
+    a = alpha_star(p) * 2
+    with G.Gadi.from_problem(p) as H:
+        xh = np.zeros(p.nvec)
+        st1, s1 = H.solve(b, xh, a, 1.0, FP32, 1e-10, 2000)
+        xd = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+        st2, s2 = H.solve(dev64(b), xd, a, 1.0, FP32, 1e-10, 2000)
+        xd2 = torch.zeros_like(xd)
+        st3, s3 = H.solve(dev64(b), xd2, a, 1.0, FP32, 1e-10, 2000)
+    assert st1 == st2 == st3 == G.OK
+    assert np.array_equal(xh, xd.cpu().numpy())
+    assert torch.equal(xd, xd2)
+    assert s1["outer_its"] == s2["outer_its"] == s3["outer_its"]
+    assert s1["inner_its_h"] == s2["inner_its_h"]
+
+
+def test_argument_validation_and_edge_cases():
+    import torch
+    p, xt = conv_diff_2d(16, 206)
+    b = O.Oracle(p).rhs(xt)
+    with G.Gadi.from_problem(p) as H:
+        x = np.zeros(p.nvec)
+        for kw in [dict(alpha=0.0), dict(alpha=-1.0), dict(omega=2.0), dict(omega=-0.1)]:
+            args = dict(alpha=0.5, omega=1.0)
+            args.update(kw)
+            st, _ = H.solve(b, x, args["alpha"], args["omega"], FP32, 1e-10, 10, check=False)
+            assert st == G.ERR_INVALID
+        bn = b.copy()
+        bn[3] = np.nan
+        st, _ = H.solve(bn, x, 0.5, 1.0, FP32, 1e-10, 10, check=False)
+        assert st == G.ERR_NONFINITE
+        st, _ = H.solve(dev64(bn), torch.zeros(p.nvec, dtype=torch.float64, device="cuda"), 0.5,
+                        1.0, FP32, 1e-10, 10, check=False)
+        assert st == G.ERR_NONFINITE
+        assert np.all(x == 0)
+        # maxit = 0: one residual, no update
+        x0 = np.full(p.nvec, 0.25)
+        st, s = H.solve(b, x0, 0.5, 1.0, FP32, 1e-10, 0)
+        assert st == G.NOT_CONVERGED and s["outer_its"] == 0 and np.all(x0 == 0.25)
+        # b = 0 with x0 = 0: already solved
+        z = np.zeros(p.nvec)
+        st, s = H.solve(np.zeros(p.nvec), z, 0.5, 1.0, BF16, 1e-10, 10)
+        assert st == G.OK and s["outer_its"] == 0 and np.all(z == 0)
+    with pytest.raises(G.GadiError):
+        G.Gadi(G.STENCIL_2D5, 0, 5)
+    with pytest.raises(G.GadiError):
+        G.Gadi(G.CSR, rowptr=[0, 1], col=[3], val=[1.0])
+
+
+def test_norm2_estimate():
+    p, xt = conv_diff_2d(20, 207, ny=17)
+    orc = O.Oracle(p)
+    A = orc.dense(O.OP_A)
+    with G.Gadi.from_problem(p) as H:
+        est = H.norm2(200)
+    true = np.linalg.norm(A, 2)
+    assert 0.999 * true <= est <= true * (1 + 1e-10)
