@@ -126,7 +126,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     B.build()
-    p, xt = config2(args.n)
+    p, xt = config2(args.grid)
     alpha = ALPHA_FACTOR * alpha_star(p)
     n = p.nvec
     H = G.Gadi.from_problem(p)
@@ -247,6 +247,28 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+def run_profile_case(args):
+    """A small, bounded launch for ncu: one solve of the benchmark workload
+    capped at --maxit outer iterations (the first kernel launch is the FP64
+    operator application that forms b; the solve is the second)."""
+    import torch
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import alpha_star, config2
+    B.build()
+    prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[args.profile_case]
+    p, xt = config2(args.grid)
+    H = G.Gadi.from_problem(p)
+    xtd = torch.from_numpy(xt).cuda()
+    b = torch.zeros_like(xtd)
+    H.apply(G.OP_A, xtd, b)
+    x = torch.zeros_like(b)
+    st, s = H.solve(b, x, ALPHA_FACTOR * alpha_star(p), OMEGA, prec, TOL, args.maxit,
+                    tol_h=TOL_INNER, tol_s=TOL_INNER)
+    print(json.dumps({"profile_case": args.profile_case, "status": G.status_str(st), **s}))
+
+
 def cpu_baseline(p, xt, alpha, gpu_stats, outer):
     """The CPU oracle timed on a bounded sample: `outer` outer iterations of
     Algorithm 1 (FP64 outer, FP32 inner) on the full grid, scaled to the
@@ -271,7 +293,7 @@ def run_reference(args):
     if rank != 0:
         return
     from workloads import alpha_star, config2
-    p, xt = config2(args.n)
+    p, xt = config2(args.grid)
     alpha = ALPHA_FACTOR * alpha_star(p)
     counts = {"outer_its": args.ref_outer}
     try:
@@ -303,15 +325,19 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--maxit", type=int, default=MAXIT)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-outer", type=int, default=1)
     ap.add_argument("--ref-outer", type=int, default=2800)
+    ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
+                    help="run one solve capped at --maxit outer iterations (for ncu) and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

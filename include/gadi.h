@@ -139,6 +139,11 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low);
 /* Human-readable name of a status code (static string). */
 const char *gadi_status_str(gadi_status s);
 
+/* Description of the last CUDA failure seen by this thread in the library
+ * (the failing call, source line and CUDA's message); "" if none.  The
+ * string belongs to the library and is overwritten by the next failure. */
+const char *gadi_last_error(void);
+
 /* Build the operator set for a problem and a splitting (Sec. 3.1) on the
  * current CUDA device.  Stencils are matrix-free: only scalars are kept.
  * CSR: A, M = (A + A^T)/2 and N = (A - A^T)/2 are formed in FP64 on the host

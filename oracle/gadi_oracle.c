@@ -25,6 +25,8 @@
  *   carried in the compute type (double for FP64, float otherwise).
  *   FP32 arithmetic is C float arithmetic (IEEE binary32, round to nearest
  *   even; build with -ffp-contract=off so no fused multiply-add is formed).
+ *   FP64 operator products are accumulated with C99 fma() (one rounding per
+ *   neighbour term, in the fixed order below), as are the FP64 CG updates.
  *   BF16 rounding is written out from its definition: round to nearest, ties
  *   to even, at 8 significant bits with the binary32 exponent range.
  *
@@ -163,14 +165,15 @@ static long nbr(const orc_op *op, int ix, int iy, int iz, int dir)
     return ((long)iz * ny + iy) * nx + ix;
 }
 
-/* y = Op x in double, fixed summation order. */
+/* y = Op x in double, fixed summation order, each neighbour term added
+ * with a fused multiply-add: s = d x_i, then s = fma(c_dir, x_nbr, s). */
 static void apply_d(const orc_op *op, const double *x, double *y)
 {
     if (op->kind == ORC_K_CSR) {
         for (int i = 0; i < op->n; i++) {
             double s = op->d * x[i];
             for (int k = op->rowptr[i]; k < op->rowptr[i + 1]; k++)
-                s = s + op->val[k] * x[op->col[k]];
+                s = fma(op->val[k], x[op->col[k]], s);
             y[i] = s;
         }
         return;
@@ -186,7 +189,7 @@ static void apply_d(const orc_op *op, const double *x, double *y)
                     double s = op->d * x[i];
                     for (int dir = 0; dir < ndir; dir++) {
                         long j = nbr(op, ix, iy, iz, dir);
-                        if (j >= 0) s = s + op->c[dir] * x[j];
+                        if (j >= 0) s = fma(op->c[dir], x[j], s);
                     }
                     y[i] = s;
                 } else {
@@ -194,13 +197,13 @@ static void apply_d(const orc_op *op, const double *x, double *y)
                     for (int dir = 0; dir < ndir; dir++) {
                         long j = nbr(op, ix, iy, iz, dir);
                         if (j >= 0) {
-                            sr = sr + op->c[dir] * x[2 * j];
-                            si = si + op->c[dir] * x[2 * j + 1];
+                            sr = fma(op->c[dir], x[2 * j], sr);
+                            si = fma(op->c[dir], x[2 * j + 1], si);
                         }
                     }
                     /* (i e) (xr + i xi) = -e xi + i e xr */
-                    sr = sr - op->e * x[2 * i + 1];
-                    si = si + op->e * x[2 * i];
+                    sr = fma(-op->e, x[2 * i + 1], sr);
+                    si = fma(op->e, x[2 * i], si);
                     y[2 * i] = sr;
                     y[2 * i + 1] = si;
                 }
@@ -436,7 +439,7 @@ static int cg_d(const orc_op *op1, const orc_op *op2, const double *rhs, double 
     for (int i = 0; i < m; i++) xsol[i] = 0.0;
     if (rr0 == 0.0) return 0;
     for (int j = 0; j < maxit; j++) {
-        for (int i = 0; i < m; i++) p[i] = (j == 0) ? r[i] : r[i] + beta * p[i];
+        for (int i = 0; i < m; i++) p[i] = (j == 0) ? r[i] : fma(beta, p[i], r[i]);
         double pq;
         if (op2 == NULL) {
             apply_d(op1, p, q);
@@ -448,8 +451,8 @@ static int cg_d(const orc_op *op1, const orc_op *op2, const double *rhs, double 
         }
         double a = rr / pq;
         for (int i = 0; i < m; i++) {
-            xsol[i] = (j == 0) ? a * p[i] : xsol[i] + a * p[i];
-            r[i] = r[i] - a * q[i];
+            xsol[i] = (j == 0) ? a * p[i] : fma(a, p[i], xsol[i]);
+            r[i] = fma(-a, q[i], r[i]);
         }
         double rn = dot_d(m, r, r);
         its = j + 1;

@@ -28,7 +28,10 @@ PREC_NAMES = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 
 class GadiError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {status_str(status)} ({status})")
+        detail = ""
+        if status in (ERR_CUDA, ERR_OOM):
+            detail = " -- " + last_error()
+        super().__init__(f"{what}: {status_str(status)} ({status}){detail}")
         self.status = status
 
 
@@ -73,6 +76,8 @@ def lib():
             L.gadi_opts_default.restype = None
             L.gadi_status_str.argtypes = [C.c_int]
             L.gadi_status_str.restype = C.c_char_p
+            L.gadi_last_error.argtypes = []
+            L.gadi_last_error.restype = C.c_char_p
             L.gadi_create.argtypes = [C.POINTER(Problem), C.c_int, C.POINTER(vp)]
             L.gadi_destroy.argtypes = [vp]
             L.gadi_destroy.restype = None
@@ -94,6 +99,10 @@ def lib():
 
 def status_str(s: int) -> str:
     return lib().gadi_status_str(int(s)).decode()
+
+
+def last_error() -> str:
+    return lib().gadi_last_error().decode()
 
 
 def _ptr(a):

@@ -37,7 +37,18 @@ def _deps_mtime() -> float:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compile (incrementally) and link libgadi.so; returns its path.  Extra
+    nvcc flags may be given in `extra` or the GADI_NVCC_FLAGS environment
+    variable (tuning experiments; a change forces a rebuild)."""
     os.makedirs(BUILD, exist_ok=True)
+    env_flags = os.environ.get("GADI_NVCC_FLAGS", "").split()
+    extra = list(extra or []) + env_flags
+    stamp = os.path.join(BUILD, "flags.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if old != " ".join(extra):
+        force = True
+        with open(stamp, "w") as f:
+            f.write(" ".join(extra))
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     dep_t = _deps_mtime()
     objs, jobs = [], []
@@ -45,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep_t):
-            jobs.append([nvcc(), *ARCH, *FLAGS, *(extra or []), "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

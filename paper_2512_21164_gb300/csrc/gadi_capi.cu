@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -101,11 +102,17 @@ struct gadi_handle {
 
 namespace {
 
-gadi_status cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? GADI_ERR_OOM : GADI_ERR_CUDA; }
+thread_local char g_last_error[256] = "";
+
+gadi_status cuda_err(cudaError_t e, const char *what, int line)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s (line %d): %s", what, line, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GADI_ERR_OOM : GADI_ERR_CUDA;
+}
 #define CK(call)                                                                                             \
     do {                                                                                                     \
         cudaError_t e_ = (call);                                                                             \
-        if (e_ != cudaSuccess) return cuda_err(e_);                                                          \
+        if (e_ != cudaSuccess) return cuda_err(e_, #call, __LINE__);                                          \
     } while (0)
 
 bool is_device_ptr(const void *p)
@@ -203,7 +210,19 @@ gadi_status ensure_ws(gadi_handle *h, int prec, Work *w)
     return GADI_OK;
 }
 
-template <class T> void to_storage(int prec, const std::vector<double> &v, std::vector<T> &out);
+// Every mode gets every work buffer; entry points then point the slots that
+// carry caller vectors at those.  No kernel path can meet a null work slot.
+void set_work(Params &P, const Work &w)
+{
+    P.x1 = w.x1;
+    P.r = w.r;
+    P.z = w.z;
+    P.p0 = w.p0;
+    P.p1 = w.p1;
+    P.y = w.y;
+    P.u = w.u;
+    P.q = w.q;
+}
 
 // u_s copies of H = alpha I + M, S = alpha I + N and S^T = alpha I - N on M's
 // pattern (CSR only); the shift is added in FP64 before rounding.
@@ -272,6 +291,14 @@ const void *pick_kernel(gadi_handle *h, int prec, bool aligned)
 
 gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStream_t st, int *blocks_out)
 {
+    // refuse to launch with a null slot the mode dereferences
+    if (P.mode == MODE_SOLVE || P.mode == MODE_SOLVE_H || P.mode == MODE_SOLVE_S) {
+        if (!P.r || !P.z || !P.p0 || !P.p1 || !P.y || !P.u || (h->kind == GADI_CSR && !P.q))
+            return GADI_ERR_INVALID;
+    }
+    if ((P.mode == MODE_SOLVE || P.mode == MODE_RESIDUAL) && (!P.b || !P.x || !P.x1 || !P.r))
+        return GADI_ERR_INVALID;
+    if (P.mode == MODE_APPLY && (!P.ax_in || !P.ax_out)) return GADI_ERR_INVALID;
     const bool al = params_aligned(P);
     if (!al && h->kind == GADI_COMPLEX_2D5) return GADI_ERR_INVALID; // complex vectors: 16-byte aligned
     const void *k = pick_kernel(h, prec, al);
@@ -477,6 +504,8 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->hist = nullptr;
 }
 
+const char *gadi_last_error(void) { return g_last_error; }
+
 const char *gadi_status_str(gadi_status s)
 {
     switch (s) {
@@ -599,6 +628,7 @@ gadi_status gadi_create(const gadi_problem *p, gadi_splitting split, gadi_handle
             if (!ok) st = GADI_ERR_OOM;
         }
     }
+    if (st == GADI_OK) st = ensure_ctl(h, 1, 1);
     if (st != GADI_OK) {
         gadi_destroy(h);
         return st;
@@ -669,8 +699,7 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
     P.mode = MODE_SOLVE;
     P.b = db;
     P.x = dx;
-    P.x1 = w.x1;
-    P.r = w.r; P.z = w.z; P.p0 = w.p0; P.p1 = w.p1; P.y = w.y; P.u = w.u; P.q = w.q;
+    set_work(P, w);
     P.tol = tol;
     P.tol_h = o.tol_h;
     P.tol_s = o.tol_s;
@@ -773,6 +802,7 @@ gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b,
     Params P;
     fill_base(h, P, prec);
     P.mode = MODE_RESIDUAL;
+    set_work(P, w);
     P.b = b;
     P.x = (double *)x;
     P.y = (void *)y;
@@ -802,7 +832,8 @@ gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, con
     fill_base(h, P, prec);
     fill_inner(h, P, prec, alpha, 1.0);
     P.mode = MODE_SOLVE_H;
-    P.r = w.r; P.z = z; P.p0 = w.p0; P.p1 = w.p1; P.q = w.q;
+    set_work(P, w);
+    P.z = z;
     P.tol_h = tol;
     P.maxit_inner = maxit;
     P.inner_stag = stag;
@@ -830,7 +861,9 @@ gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_p
     fill_base(h, P, prec);
     fill_inner(h, P, prec, alpha, omega);
     P.mode = MODE_SOLVE_S;
-    P.z = (void *)z; P.y = y; P.r = w.r; P.u = w.u; P.p0 = w.p0; P.p1 = w.p1; P.q = w.q;
+    set_work(P, w);
+    P.z = (void *)z;
+    P.y = y;
     P.tol_s = tol;
     P.maxit_inner = maxit;
     P.inner_stag = stag;

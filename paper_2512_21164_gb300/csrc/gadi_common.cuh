@@ -72,27 +72,36 @@ template <> struct Prec<P_BF16> {
 // vector loads / stores of W consecutive elements (W * sizeof(T) in
 // {2,4,8,16,32,64} bytes; the address must be aligned to min(16, that size))
 // ---------------------------------------------------------------------------
+// Loads come in two cache policies: `load` (ld.global.cg, L2 only) for data a
+// block touches once per phase, and `load_ca` (ld.global.ca, L1 and L2) for
+// stencil inputs whose rows neighbouring warps of the same block also read.
+// Every buffer read with load_ca is read-only during the phase that reads it;
+// the grid barrier between phases (acquire at gpu scope) orders it after the
+// writes of the previous phase.
 template <class T, int W> struct VecIO {
     static constexpr int BYTES = W * (int)sizeof(T);
-    __device__ static void load(const T *p, T (&v)[W])
+    template <bool CA>
+    __device__ static void load_p(const T *p, T (&v)[W])
     {
         if constexpr (BYTES >= 16) {
 #pragma unroll
             for (int i = 0; i < BYTES / 16; i++) {
-                uint4 q = __ldcg(reinterpret_cast<const uint4 *>(p) + i);
-                reinterpret_cast<uint4 *>(v)[i] = q;
+                const uint4 *a = reinterpret_cast<const uint4 *>(p) + i;
+                reinterpret_cast<uint4 *>(v)[i] = CA ? __ldca(a) : __ldcg(a);
             }
         } else if constexpr (BYTES == 8) {
-            uint2 q = __ldcg(reinterpret_cast<const uint2 *>(p));
-            reinterpret_cast<uint2 *>(v)[0] = q;
+            const uint2 *a = reinterpret_cast<const uint2 *>(p);
+            reinterpret_cast<uint2 *>(v)[0] = CA ? __ldca(a) : __ldcg(a);
         } else if constexpr (BYTES == 4) {
-            unsigned q = __ldcg(reinterpret_cast<const unsigned *>(p));
-            reinterpret_cast<unsigned *>(v)[0] = q;
+            const unsigned *a = reinterpret_cast<const unsigned *>(p);
+            reinterpret_cast<unsigned *>(v)[0] = CA ? __ldca(a) : __ldcg(a);
         } else {
-            unsigned short q = __ldcg(reinterpret_cast<const unsigned short *>(p));
-            reinterpret_cast<unsigned short *>(v)[0] = q;
+            const unsigned short *a = reinterpret_cast<const unsigned short *>(p);
+            reinterpret_cast<unsigned short *>(v)[0] = CA ? __ldca(a) : __ldcg(a);
         }
     }
+    __device__ static void load(const T *p, T (&v)[W]) { load_p<false>(p, v); }
+    __device__ static void load_ca(const T *p, T (&v)[W]) { load_p<true>(p, v); }
     __device__ static void store(T *p, const T (&v)[W])
     {
         if constexpr (BYTES >= 16) {
@@ -175,18 +184,21 @@ struct GridSync {
 // ---------------------------------------------------------------------------
 // deterministic reductions
 // ---------------------------------------------------------------------------
-// Each block reduces NV per-thread partial sums (double) in a fixed tree and
+// Each block reduces NV per-thread partial sums (type RT) in a fixed tree and
 // writes them to part[k * G + blockIdx.x].  After a grid barrier every block
 // reads all G partials and sums them in the same fixed order, so every block
 // holds bitwise identical totals and takes identical control decisions.
-template <int NV>
-__device__ __forceinline__ void block_partials_write(double (&v)[NV], double *part, int G)
+// RT is float for the FP32/BF16 inner solves (FP64 throughput on this GPU is
+// about 1/60 of FP32, so double arithmetic on every thread would dominate a
+// reduction) and double for FP64 sums (the outer residual norm, GADI-FP64).
+template <int NV, class RT>
+__device__ __forceinline__ void block_partials_write(const RT (&v)[NV], RT *part, int G)
 {
-    __shared__ double red[NV][32];
+    __shared__ RT red[NV][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; k++) {
-        double s = v[k];
+        RT s = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) red[k][warp] = s;
@@ -195,34 +207,38 @@ __device__ __forceinline__ void block_partials_write(double (&v)[NV], double *pa
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; k++) {
-            double s = lane < nw ? red[k][lane] : 0.0;
+            RT s = lane < nw ? red[k][lane] : RT(0);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) __stcg(part + (size_t)k * G + blockIdx.x, s);
         }
     }
-    __syncthreads();
 }
 
-template <int NV>
-__device__ __forceinline__ void grid_partials_sum(const double *part, int G, double (&out)[NV])
+template <int NV, class RT>
+__device__ __forceinline__ void grid_partials_sum(const RT *part, int G, RT (&out)[NV])
 {
-    __shared__ double red[NV][32];
-    __shared__ double res[NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < G; i += blockDim.x) s += __ldcg(part + (size_t)k * G + i);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[k][warp] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {
+    // One warp reads all G partials with independent, unrolled loads (one L2
+    // round trip), sums them in a fixed order and broadcasts through shared
+    // memory.
+    __shared__ RT res[NV];
+    constexpr int U = 8;
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < NV; k++) {
-            double s = lane < nw ? red[k][lane] : 0.0;
+            const RT *pk = part + (size_t)k * G;
+            RT s = RT(0);
+            for (int base = lane; base < G; base += 32 * U) {
+                RT t[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = base + 32 * u;
+                    t[u] = i < G ? __ldcg(pk + i) : RT(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) s += t[u];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) res[k] = s;

@@ -21,13 +21,17 @@
 namespace gadi {
 
 constexpr int kThreads = 256;
+// resident blocks per SM the register budget is sized for (256 threads each)
+#ifndef GADI_MIN_BLOCKS
+#define GADI_MIN_BLOCKS 2
+#endif
 
 // ---------------------------------------------------------------------------
 // arithmetic policies
 // ---------------------------------------------------------------------------
 // Exact: every product and sum rounded separately, in the operation order of
 // the method's definition (no contraction into FMA).  Used for FP32/BF16
-// arithmetic and for the FP64 residual / operator application.
+// arithmetic.
 template <class C> struct ArExact;
 template <> struct ArExact<float> {
     __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
@@ -41,13 +45,15 @@ template <> struct ArExact<double> {
     __device__ static double madd(double a, double b, double s) { return __dadd_rn(s, __dmul_rn(a, b)); }
     __device__ static double div(double a, double b) { return __ddiv_rn(a, b); }
 };
-// Fused: products folded into FMA.  Used for the all-FP64 inner solves, where
-// the FP64 pipe, not memory, is the scarcer resource on this GPU.
+// Fused: every product added with one fused multiply-add, in the same order.
+// Used for all FP64 arithmetic (the residual, operator application, GADI-FP64
+// inner solves): the FP64 pipe, not memory, is the scarcer resource on this
+// GPU.  Plain products and quotients are rounded separately.
 struct ArFusedD {
-    __device__ static double mul(double a, double b) { return a * b; }
-    __device__ static double add(double a, double b) { return a + b; }
+    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
     __device__ static double madd(double a, double b, double s) { return fma(a, b, s); }
-    __device__ static double div(double a, double b) { return a / b; }
+    __device__ static double div(double a, double b) { return __ddiv_rn(a, b); }
 };
 template <int PREC> struct InnerAr { using T = ArExact<float>; };
 template <> struct InnerAr<P_FP64> { using T = ArFusedD; };
@@ -81,31 +87,145 @@ template <class C> struct Coef7 {
 };
 
 // ---------------------------------------------------------------------------
+// fields: the stencil input of a phase, computed from raw loads
+// ---------------------------------------------------------------------------
+// A field turns the raw 16-byte loads of N consecutive elements into N values
+// of its type FT.  Raw data of a row are loaded PD rows before they are used,
+// so the loads are split from the arithmetic: load<N>() fills a Raw<N>,
+// value<N>() computes the field from it.  A zero Raw gives a zero field
+// (Dirichlet value outside the grid).
+
+// x + y in FP64 (the update fused into the residual); y may be absent
+template <int PREC>
+struct FieldX {
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using FT = double;
+    const double *x;
+    const S *y;
+    template <int N> struct Raw {
+        double x[N];
+        S y[N];
+    };
+    template <int N> __device__ void load(long long g, Raw<N> &r) const
+    {
+        VecIO<double, N>::load_ca(x + g, r.x);
+        if (y) VecIO<S, N>::load_ca(y + g, r.y);
+    }
+    template <int N> __device__ void value(const Raw<N> &r, double (&o)[N]) const
+    {
+#pragma unroll
+        for (int v = 0; v < N; v++) o[v] = y ? __dadd_rn(r.x[v], PT::to_f64(r.y[v])) : r.x[v];
+    }
+};
+
+// fl_s(src + beta p_old) (the CG direction update), or src on the first step
+template <int PREC>
+struct FieldDir {
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using FT = C;
+    using A = typename InnerAr<PREC>::T;
+    const S *src, *pold;
+    C beta;
+    bool first;
+    template <int N> struct Raw {
+        S s[N], p[N];
+    };
+    template <int N> __device__ void load(long long g, Raw<N> &r) const
+    {
+        VecIO<S, N>::load_ca(src + g, r.s);
+        if (!first) VecIO<S, N>::load_ca(pold + g, r.p);
+    }
+    template <int N> __device__ void value(const Raw<N> &r, C (&o)[N]) const
+    {
+#pragma unroll
+        for (int v = 0; v < N; v++)
+            o[v] = first ? PT::ld(r.s[v]) : PT::ld(PT::st(A::madd(beta, PT::ld(r.p[v]), PT::ld(r.s[v]))));
+    }
+};
+
+// a stored u_s vector, optionally scaled and re-rounded: fl_s(scale v)
+template <int PREC, bool SCALE>
+struct FieldLoad {
+    using PT = Prec<PREC>;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using FT = C;
+    using A = typename InnerAr<PREC>::T;
+    const S *src;
+    C scale;
+    template <int N> struct Raw {
+        S s[N];
+    };
+    template <int N> __device__ void load(long long g, Raw<N> &r) const { VecIO<S, N>::load_ca(src + g, r.s); }
+    template <int N> __device__ void value(const Raw<N> &r, C (&o)[N]) const
+    {
+#pragma unroll
+        for (int v = 0; v < N; v++) {
+            if constexpr (SCALE) o[v] = PT::ld(PT::st(A::mul(scale, PT::ld(r.s[v]))));
+            else o[v] = PT::ld(r.s[v]);
+        }
+    }
+};
+
+// own-point inputs: NV vectors of type T at the output row
+template <class T, int W, int NV>
+struct OwnIn {
+    T v[NV > 0 ? NV : 1][W];
+};
+
+template <class R, bool D3> struct YNbr {
+    R s, n;
+};
+template <class R> struct YNbr<R, false> {};
+
+// ---------------------------------------------------------------------------
 // the marching sweep over a 2D or 3D grid
 // ---------------------------------------------------------------------------
 // A warp owns a strip of 32*W consecutive elements of a row (W per lane) and
 // marches along the slowest axis (y in 2D, z in 3D) over a contiguous range
-// of its work units, keeping the field at m-1, m, m+1 in registers.  x
-// neighbours come from warp shuffles (lane 0 / 31 evaluate the field one
-// element past the strip); 3D y neighbours are evaluated directly.  The field
-// is zero outside the grid (Dirichlet).  Work units are split evenly and
-// contiguously over all warps of the grid.
-// field values of W consecutive elements at g, or zeros when `valid` is false
-template <int W, class Ph>
-__device__ __forceinline__ void load_row(const Ph &ph, bool valid, long long g, typename Ph::FT (&o)[W])
+// of work units, keeping the field at rows m-1, m, m+1 in registers.  The raw
+// loads of row m+PD+1 are issued while row m is computed (a ring of PD+1
+// prefetched rows), so every warp keeps several rows of loads in flight.
+// x neighbours come from warp shuffles; lanes 0 / 31 load the K elements just
+// past the strip; 3D y neighbours are loaded with the row.  Outside the grid
+// the field is zero (Dirichlet).  Work units are split evenly and contiguously
+// over all warps of the grid.
+template <class Ph, int W, int K, bool D3>
+struct Slot {
+    using F = typename Ph::Fld;
+    typename F::template Raw<W> c;
+    typename F::template Raw<K> hl, hr;
+    typename Ph::Own o;
+    YNbr<typename F::template Raw<W>, D3> y;
+};
+
+// Load the raw data of row g into a slot.  Invalid rows (outside the grid)
+// get a zero field; halo raws are written only for the lanes that use them
+// (lane 0 / 31), own-point raws only for rows the warp outputs.
+template <int W, int K, bool D3, class Ph>
+__device__ __forceinline__ void load_slot(const Ph &ph, Slot<Ph, W, K, D3> &sl, bool valid, bool own,
+                                          long long g, int lane, int e0, int ne, int yy, int ny)
 {
-    if (valid) {
-        ph.fv(g, o);
-    } else {
-#pragma unroll
-        for (int v = 0; v < W; v++) o[v] = typename Ph::FT(0);
+    sl = Slot<Ph, W, K, D3>{};
+    if (!valid) return;
+    ph.f.template load<W>(g, sl.c);
+    if (lane == 0 && e0 > 0) ph.f.template load<K>(g - K, sl.hl);
+    if (lane == 31 && e0 + W < ne) ph.f.template load<K>(g + W, sl.hr);
+    if (own) ph.load_own(g, sl.o);
+    if constexpr (D3) {
+        if (yy > 0) ph.f.template load<W>(g - ne, sl.y.s);
+        if (yy + 1 < ny) ph.f.template load<W>(g + ne, sl.y.n);
     }
 }
 
-template <int W, int K, bool D3, class Ph, class AT>
+template <int W, int K, bool D3, int PD, class Ph, class AT>
 __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2])
 {
-    using FT = typename Ph::FT;
+    using FT = typename Ph::Fld::FT;
+    using SL = Slot<Ph, W, K, D3>;
     const int lane = threadIdx.x & 31;
     const int nstrips = (ne + 32 * W - 1) / (32 * W);
     const int collen = D3 ? nz : ny;
@@ -126,26 +246,37 @@ __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (
         const int e0 = strip * 32 * W + lane * W;
         const bool act = e0 < ne;
         const long long cbase = (D3 ? (long long)yy * ne : 0ll) + e0;
+
+        typename Ph::Fld::template Raw<W> rdn{};
+        if (act && m0 > 0) ph.f.template load<W>(cbase + (long long)(m0 - 1) * mstride, rdn);
+        SL ring[PD + 1];
+#pragma unroll
+        for (int i = 0; i <= PD; i++) {
+            const int m = m0 + i;
+            load_slot<W, K, D3>(ph, ring[i], act && m < collen, m < m1, cbase + (long long)m * mstride, lane,
+                                e0, ne, yy, ny);
+        }
         FT dn[W], cu[W], up[W];
-        load_row<W>(ph, act && m0 - 1 >= 0, cbase + (long long)(m0 - 1) * mstride, dn);
-        load_row<W>(ph, act, cbase + (long long)m0 * mstride, cu);
+        ph.f.template value<W>(rdn, dn);
+        ph.f.template value<W>(ring[0].c, cu);
         for (int m = m0; m < m1; ++m) {
-            load_row<W>(ph, act && m + 1 < collen, cbase + (long long)(m + 1) * mstride, up);
-            const long long g = cbase + (long long)m * mstride;
+            // ring[0] = row m, ring[1] = row m+1, ..., ring[PD] = row m+PD
+            SL nxt;
+            {
+                const int mn = m + PD + 1;
+                load_slot<W, K, D3>(ph, nxt, act && mn < collen, mn < m1, cbase + (long long)mn * mstride, lane,
+                                    e0, ne, yy, ny);
+            }
+            ph.f.template value<W>(ring[PD >= 1 ? 1 : 0].c, up);
+            if constexpr (PD == 0) ph.f.template value<W>(nxt.c, up);
             FT lh[K], rh[K];
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 lh[k] = __shfl_up_sync(0xffffffffu, cu[W - K + k], 1);
                 rh[k] = __shfl_down_sync(0xffffffffu, cu[k], 1);
             }
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < K; k++) lh[k] = (act && e0 > 0) ? ph.f1(g - K + k) : FT(0);
-            }
-            if (lane == 31) {
-#pragma unroll
-                for (int k = 0; k < K; k++) rh[k] = (act && e0 + W < ne) ? ph.f1(g + W + k) : FT(0);
-            }
+            if (lane == 0) ph.f.template value<K>(ring[0].hl, lh);
+            if (lane == 31) ph.f.template value<K>(ring[0].hr, rh);
             FT w[W], e[W];
 #pragma unroll
             for (int v = 0; v < W; v++) {
@@ -153,15 +284,19 @@ __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (
                 e[v] = (v + K < W) ? cu[v + K] : rh[v + K - W];
             }
             if (act) {
+                const long long g = cbase + (long long)m * mstride;
                 if constexpr (D3) {
                     FT sy[W], ny_[W];
-                    load_row<W>(ph, yy > 0, g - ne, sy);
-                    load_row<W>(ph, yy + 1 < ny, g + ne, ny_);
-                    ph.out(g, cu, w, e, sy, ny_, dn, up, acc);
+                    ph.f.template value<W>(ring[0].y.s, sy);
+                    ph.f.template value<W>(ring[0].y.n, ny_);
+                    ph.out(g, ring[0].o, cu, w, e, sy, ny_, dn, up, acc);
                 } else {
-                    ph.out(g, cu, w, e, dn, up, dn, up, acc);
+                    ph.out(g, ring[0].o, cu, w, e, dn, up, dn, up, acc);
                 }
             }
+#pragma unroll
+            for (int i = 0; i < PD; i++) ring[i] = ring[i + 1];
+            ring[PD] = nxt;
 #pragma unroll
             for (int v = 0; v < W; v++) {
                 dn[v] = cu[v];
@@ -172,40 +307,31 @@ __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (
 }
 
 // ---------------------------------------------------------------------------
-// stencil phases
+// stencil phases (field + own-point inputs + output)
 // ---------------------------------------------------------------------------
+// R: x_out = x + y, r = b - A x_out (FP64), r_s = fl_s(r); sums ||r||^2 and
+// ||r_s||^2.  With b == nullptr it is the operator application x_out = A x.
 template <int PREC, int W, int K, bool D3>
-struct PhResidual { // R (and MODE_APPLY with b == nullptr, y == nullptr)
+struct PhResidual {
     using PT = Prec<PREC>;
     using S = typename PT::S;
-    using FT = double;
-    using A = ArExact<double>;
-    const double *x;
-    const S *y;
+    using A = ArFusedD; // FP64 products accumulated by fused multiply-add
+    using Fld = FieldX<PREC>;
+    using Own = OwnIn<double, W, 1>;
+    Fld f;
     double *xo;
     const double *b;
     double *rout;
     S *rs;
     Coef7<double> cf;
-    __device__ double f1(long long g) const
+    __device__ void load_own(long long g, Own &o) const
     {
-        double v = __ldcg(x + g);
-        if (y) v = A::add(v, PT::to_f64(y[g]));
-        return v;
+        if (b) VecIO<double, W>::load(b + g, o.v[0]);
     }
-    __device__ void fv(long long g, double (&o)[W]) const
-    {
-        VecIO<double, W>::load(x + g, o);
-        if (y) {
-            S yv[W];
-            VecIO<S, W>::load(y + g, yv);
-#pragma unroll
-            for (int v = 0; v < W; v++) o[v] = A::add(o[v], PT::to_f64(yv[v]));
-        }
-    }
-    __device__ void out(long long g, const double (&c)[W], const double (&w)[W], const double (&e)[W],
-                        const double (&s)[W], const double (&n)[W], const double (&bb)[W],
-                        const double (&t)[W], double (&acc)[2]) const
+    template <class AT>
+    __device__ void out(long long g, const Own &o, const double (&c)[W], const double (&w)[W],
+                        const double (&e)[W], const double (&s)[W], const double (&n)[W],
+                        const double (&bb)[W], const double (&t)[W], AT (&acc)[2]) const
     {
         double ax[W];
 #pragma unroll
@@ -216,12 +342,11 @@ struct PhResidual { // R (and MODE_APPLY with b == nullptr, y == nullptr)
             VecIO<double, W>::store(xo + g, ax);
             return;
         }
-        double bv[W], r[W];
+        double r[W];
         S so[W];
-        VecIO<double, W>::load(b + g, bv);
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            r[v] = __dsub_rn(bv[v], ax[v]);
+            r[v] = __dsub_rn(o.v[0][v], ax[v]);
             acc[0] = fma(r[v], r[v], acc[0]);
             so[v] = PT::from_f64(r[v]);
             const double sv = PT::to_f64(so[v]);
@@ -233,115 +358,70 @@ struct PhResidual { // R (and MODE_APPLY with b == nullptr, y == nullptr)
     }
 };
 
-// p = fl_s(src + beta p_old) as a field (src = r for H1, t for S1)
-template <int PREC, int W>
-struct FieldDir {
+// H1: p = fl_s(r + beta p_old); sum p.(H p).  With STORE_Q (all-FP64 inner
+// arithmetic, where the FP64 pipe is the bottleneck) H p is also written out
+// so that H2 needs no stencil.
+template <int PREC, int W, int K, bool D3, bool STORE_Q>
+struct PhH1 {
     using PT = Prec<PREC>;
     using S = typename PT::S;
     using C = typename PT::C;
     using A = typename InnerAr<PREC>::T;
-    const S *src, *pold;
-    C beta;
-    bool first;
-    __device__ C f1(long long g) const
-    {
-        C v = PT::ld(src[g]);
-        if (!first) v = A::madd(beta, PT::ld(pold[g]), v);
-        return PT::ld(PT::st(v));
-    }
-    __device__ void fv(long long g, C (&o)[W]) const
-    {
-        S sv[W];
-        VecIO<S, W>::load(src + g, sv);
-        if (first) {
-#pragma unroll
-            for (int v = 0; v < W; v++) o[v] = PT::ld(sv[v]);
-        } else {
-            S pv[W];
-            VecIO<S, W>::load(pold + g, pv);
-#pragma unroll
-            for (int v = 0; v < W; v++) o[v] = PT::ld(PT::st(A::madd(beta, PT::ld(pv[v]), PT::ld(sv[v]))));
-        }
-    }
-};
-
-// plain u_s field, optionally scaled and re-rounded: fl_s(scale * v)
-template <int PREC, int W, bool SCALE>
-struct FieldLoad {
-    using PT = Prec<PREC>;
-    using S = typename PT::S;
-    using C = typename PT::C;
-    using A = typename InnerAr<PREC>::T;
-    const S *src;
-    C scale;
-    __device__ C f1(long long g) const
-    {
-        if constexpr (SCALE) return PT::ld(PT::st(A::mul(scale, PT::ld(src[g]))));
-        else return PT::ld(src[g]);
-    }
-    __device__ void fv(long long g, C (&o)[W]) const
-    {
-        S sv[W];
-        VecIO<S, W>::load(src + g, sv);
-#pragma unroll
-        for (int v = 0; v < W; v++) {
-            if constexpr (SCALE) o[v] = PT::ld(PT::st(A::mul(scale, PT::ld(sv[v]))));
-            else o[v] = PT::ld(sv[v]);
-        }
-    }
-};
-
-template <int PREC, int W, int K, bool D3>
-struct PhH1 : FieldDir<PREC, W> { // p = fl_s(r + beta p_old); sum p.(H p)
-    using Base = FieldDir<PREC, W>;
-    using C = typename Base::C;
-    using S = typename Base::S;
-    using PT = Prec<PREC>;
-    using FT = C;
-    using AT = typename AccT<PREC>::T;
+    using Fld = FieldDir<PREC>;
+    using Own = OwnIn<S, W, 0>;
+    Fld f;
     S *pnew;
+    S *qout;
     Coef7<C> h;
-    __device__ void out(long long g, const C (&c)[W], const C (&w)[W], const C (&e)[W], const C (&s)[W],
-                        const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
+    __device__ void load_own(long long, Own &) const {}
+    template <class AT>
+    __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+                        const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
     {
-        S ps[W];
+        S ps[W], qs[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<typename Base::A, C, D3, false>(h.d, h.c, C(0), c[v], w[v], e[v], s[v],
-                                                                  n[v], b[v], t[v], C(0), false);
+            const C q = stencil_at<A, C, D3, false>(h.d, h.c, C(0), c[v], w[v], e[v], s[v], n[v], b[v], t[v],
+                                                    C(0), false);
             acc[0] += (AT)c[v] * (AT)q;
             ps[v] = PT::st(c[v]);
+            qs[v] = PT::st(q);
         }
         VecIO<S, W>::store(pnew + g, ps);
+        if constexpr (STORE_Q) VecIO<S, W>::store(qout + g, qs);
     }
 };
 
+// H2: z = fl_s(z + a p), r = fl_s(r - a H p) with H p recomputed; sum r.r
 template <int PREC, int W, int K, bool D3>
-struct PhH2 : FieldLoad<PREC, W, false> { // z += a p, r -= a H p; sum r.r
-    using Base = FieldLoad<PREC, W, false>;
-    using C = typename Base::C;
-    using S = typename Base::S;
+struct PhH2 {
     using PT = Prec<PREC>;
-    using FT = C;
-    using AT = typename AccT<PREC>::T;
-    using A = typename Base::A;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    using Fld = FieldLoad<PREC, false>;
+    using Own = OwnIn<S, W, 2>; // z, r
+    Fld f;
     S *z, *r;
     C a;
     bool first;
     Coef7<C> h;
-    __device__ void out(long long g, const C (&c)[W], const C (&w)[W], const C (&e)[W], const C (&s)[W],
-                        const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
+    __device__ void load_own(long long g, Own &o) const
+    {
+        if (!first) VecIO<S, W>::load(z + g, o.v[0]);
+        VecIO<S, W>::load(r + g, o.v[1]);
+    }
+    template <class AT>
+    __device__ void out(long long g, const Own &o, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+                        const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
     {
         S zv[W], rv[W];
-        if (!first) VecIO<S, W>::load(z + g, zv);
-        VecIO<S, W>::load(r + g, rv);
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, false>(h.d, h.c, C(0), c[v], w[v], e[v], s[v], n[v], b[v],
-                                                    t[v], C(0), false);
-            const C zn = first ? A::mul(a, c[v]) : A::madd(a, c[v], PT::ld(zv[v]));
-            zv[v] = PT::st(zn);
-            rv[v] = PT::st(A::madd(-a, q, PT::ld(rv[v])));
+            const C q = stencil_at<A, C, D3, false>(h.d, h.c, C(0), c[v], w[v], e[v], s[v], n[v], b[v], t[v],
+                                                    C(0), false);
+            zv[v] = PT::st(first ? A::mul(a, c[v]) : A::madd(a, c[v], PT::ld(o.v[0][v])));
+            rv[v] = PT::st(A::madd(-a, q, PT::ld(o.v[1][v])));
             const C rr = PT::ld(rv[v]);
             acc[0] += (AT)rr * (AT)rr;
         }
@@ -350,25 +430,28 @@ struct PhH2 : FieldLoad<PREC, W, false> { // z += a p, r -= a H p; sum r.r
     }
 };
 
+// S0: t = fl_s(S^T fl_s(gamma z)); sum t.t
 template <int PREC, int W, int K, bool D3>
-struct PhS0 : FieldLoad<PREC, W, true> { // t = fl_s(S^T fl_s(gamma z)); sum t.t
-    using Base = FieldLoad<PREC, W, true>;
-    using C = typename Base::C;
-    using S = typename Base::S;
+struct PhS0 {
     using PT = Prec<PREC>;
-    using FT = C;
-    using AT = typename AccT<PREC>::T;
-    using A = typename Base::A;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    using Fld = FieldLoad<PREC, true>;
+    using Own = OwnIn<S, W, 0>;
+    Fld f;
     S *t;
     Coef7<C> st;
-    __device__ void out(long long g, const C (&c)[W], const C (&w)[W], const C (&e)[W], const C (&s)[W],
-                        const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
+    __device__ void load_own(long long, Own &) const {}
+    template <class AT>
+    __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+                        const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
     {
         S to[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v],
-                                                     tt[v], c[v ^ (K - 1)], (v & 1) != 0);
+            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
+                                                     c[v ^ (K - 1)], (v & 1) != 0);
             to[v] = PT::st(q);
             const C qq = PT::ld(to[v]);
             acc[0] += (AT)qq * (AT)qq;
@@ -377,25 +460,28 @@ struct PhS0 : FieldLoad<PREC, W, true> { // t = fl_s(S^T fl_s(gamma z)); sum t.t
     }
 };
 
+// S1: p = fl_s(t + beta p_old), u = fl_s(S p); sum u.u
 template <int PREC, int W, int K, bool D3>
-struct PhS1 : FieldDir<PREC, W> { // p = fl_s(t + beta p_old), u = fl_s(S p); sum u.u
-    using Base = FieldDir<PREC, W>;
-    using C = typename Base::C;
-    using S = typename Base::S;
+struct PhS1 {
     using PT = Prec<PREC>;
-    using FT = C;
-    using AT = typename AccT<PREC>::T;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    using Fld = FieldDir<PREC>;
+    using Own = OwnIn<S, W, 0>;
+    Fld f;
     S *pnew, *u;
     Coef7<C> sc;
-    __device__ void out(long long g, const C (&c)[W], const C (&w)[W], const C (&e)[W], const C (&s)[W],
-                        const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
+    __device__ void load_own(long long, Own &) const {}
+    template <class AT>
+    __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+                        const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
     {
         S ps[W], us[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<typename Base::A, C, D3, K == 2>(sc.d, sc.c, sc.e, c[v], w[v], e[v], s[v],
-                                                                   n[v], b[v], t[v], c[v ^ (K - 1)],
-                                                                   (v & 1) != 0);
+            const C q = stencil_at<A, C, D3, K == 2>(sc.d, sc.c, sc.e, c[v], w[v], e[v], s[v], n[v], b[v], t[v],
+                                                     c[v ^ (K - 1)], (v & 1) != 0);
             us[v] = PT::st(q);
             const C uu = PT::ld(us[v]);
             acc[0] += (AT)uu * (AT)uu;
@@ -406,34 +492,39 @@ struct PhS1 : FieldDir<PREC, W> { // p = fl_s(t + beta p_old), u = fl_s(S p); su
     }
 };
 
+// S2: y = fl_s(y + a p), t = fl_s(t - a S^T u); sum t.t
 template <int PREC, int W, int K, bool D3>
-struct PhS2 : FieldLoad<PREC, W, false> { // y += a p, t -= a S^T u; sum t.t
-    using Base = FieldLoad<PREC, W, false>;
-    using C = typename Base::C;
-    using S = typename Base::S;
+struct PhS2 {
     using PT = Prec<PREC>;
-    using FT = C;
-    using AT = typename AccT<PREC>::T;
-    using A = typename Base::A;
+    using S = typename PT::S;
+    using C = typename PT::C;
+    using A = typename InnerAr<PREC>::T;
+    using Fld = FieldLoad<PREC, false>;
+    using Own = OwnIn<S, W, 3>; // p, y, t
+    Fld f;
     const S *p;
     S *y, *t;
     C a;
     bool first;
     Coef7<C> st;
-    __device__ void out(long long g, const C (&c)[W], const C (&w)[W], const C (&e)[W], const C (&s)[W],
-                        const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
+    __device__ void load_own(long long g, Own &o) const
     {
-        S pv[W], yv[W], tv[W];
-        VecIO<S, W>::load(p + g, pv);
-        if (!first) VecIO<S, W>::load(y + g, yv);
-        VecIO<S, W>::load(t + g, tv);
+        VecIO<S, W>::load(p + g, o.v[0]);
+        if (!first) VecIO<S, W>::load(y + g, o.v[1]);
+        VecIO<S, W>::load(t + g, o.v[2]);
+    }
+    template <class AT>
+    __device__ void out(long long g, const Own &o, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+                        const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
+    {
+        S yv[W], tv[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v],
-                                                     tt[v], c[v ^ (K - 1)], (v & 1) != 0);
-            const C pp = PT::ld(pv[v]);
-            yv[v] = PT::st(first ? A::mul(a, pp) : A::madd(a, pp, PT::ld(yv[v])));
-            tv[v] = PT::st(A::madd(-a, q, PT::ld(tv[v])));
+            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
+                                                     c[v ^ (K - 1)], (v & 1) != 0);
+            const C pp = PT::ld(o.v[0][v]);
+            yv[v] = PT::st(first ? A::mul(a, pp) : A::madd(a, pp, PT::ld(o.v[1][v])));
+            tv[v] = PT::st(A::madd(-a, q, PT::ld(o.v[2][v])));
             const C t2 = PT::ld(tv[v]);
             acc[0] += (AT)t2 * (AT)t2;
         }
@@ -454,6 +545,8 @@ struct StencilImpl {
     using AT = typename AccT<PREC>::T;
     static constexpr int K = (KIND == K_C2D5) ? 2 : 1;
     static constexpr bool D3 = (KIND == K_3D7);
+    static constexpr bool STORE_Q = (PREC == P_FP64);
+    static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead
     const Params &P;
     int ne, ny, nz;
     Coef7<double> ca;
@@ -479,66 +572,84 @@ struct StencilImpl {
 
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
-        PhResidual<PREC, WR, K, D3> ph{xin, y, xout, P.b, P.r_out, (S *)P.r, ca};
+        PhResidual<PREC, WR, K, D3> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca};
         double a[2] = {0.0, 0.0};
-        march<WR, K, D3>(ph, ne, ny, nz, a);
+        march<WR, K, D3, PD>(ph, ne, ny, nz, a);
         acc[0] = a[0];
         acc[1] = a[1];
     }
     __device__ void apply(const double *x, double *yout) const
     {
-        PhResidual<PREC, WR, K, D3> ph{x, nullptr, yout, nullptr, nullptr, nullptr, ca};
+        PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca};
         double a[2] = {0.0, 0.0};
-        march<WR, K, D3>(ph, ne, ny, nz, a);
+        march<WR, K, D3, PD>(ph, ne, ny, nz, a);
     }
-    __device__ void h1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2]) const
+    __device__ void h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
-        PhH1<PREC, WI, K, D3> ph;
-        ph.src = (const S *)P.r; ph.pold = pold; ph.beta = beta; ph.first = first;
-        ph.pnew = pnew; ph.h = ch;
-        AT a[2] = {AT(0), AT(0)};
-        march<WI, K, D3>(ph, ne, ny, nz, a);
-        acc[0] = (double)a[0];
-        acc[1] = 0.0;
+        PhH1<PREC, WI, K, D3, STORE_Q> ph;
+        ph.f.src = (const S *)P.r; ph.f.pold = pold; ph.f.beta = beta; ph.f.first = first;
+        ph.pnew = pnew; ph.qout = (S *)P.u; ph.h = ch;
+        acc[0] = acc[1] = AT(0);
+        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
     }
-    __device__ void h2(bool first, C a_, const S *p, double (&acc)[2]) const
+    __device__ void h2(bool first, C a_, const S *p, AT (&acc)[2]) const
     {
-        PhH2<PREC, WI, K, D3> ph;
-        ph.src = p; ph.scale = C(1); ph.z = (S *)P.z; ph.r = (S *)P.r; ph.a = a_; ph.first = first;
-        ph.h = ch;
-        AT a[2] = {AT(0), AT(0)};
-        march<WI, K, D3>(ph, ne, ny, nz, a);
-        acc[0] = (double)a[0];
-        acc[1] = 0.0;
+        if constexpr (STORE_Q) {
+            // pointwise: z += a p, r -= a q with q = H p stored by H1
+            using V = VecIO<S, WI>;
+            S *z = (S *)P.z, *r = (S *)P.r;
+            const S *q = (const S *)P.u;
+            AT s = AT(0);
+            const long long nv = P.nelem / WI;
+            for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
+                 i += (long long)gridDim.x * blockDim.x) {
+                const long long g = i * WI;
+                S pv[WI], qv[WI], zv[WI], rv[WI];
+                V::load(p + g, pv);
+                V::load(q + g, qv);
+                V::load(r + g, rv);
+                if (!first) V::load(z + g, zv);
+#pragma unroll
+                for (int v = 0; v < WI; v++) {
+                    zv[v] = first ? A::mul(a_, pv[v]) : A::madd(a_, pv[v], zv[v]);
+                    rv[v] = A::madd(-a_, qv[v], rv[v]);
+                    s += (AT)rv[v] * (AT)rv[v];
+                }
+                V::store(z + g, zv);
+                V::store(r + g, rv);
+            }
+            acc[0] = s;
+            acc[1] = AT(0);
+        } else {
+            PhH2<PREC, WI, K, D3> ph;
+            ph.f.src = p; ph.f.scale = C(1);
+            ph.z = (S *)P.z; ph.r = (S *)P.r; ph.a = a_; ph.first = first; ph.h = ch;
+            acc[0] = acc[1] = AT(0);
+            march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+        }
     }
-    __device__ void s0(C gamma, double (&acc)[2]) const
+    __device__ void s0(C gamma, AT (&acc)[2]) const
     {
         PhS0<PREC, WI, K, D3> ph;
-        ph.src = (const S *)P.z; ph.scale = gamma; ph.t = (S *)P.r; ph.st = ct;
-        AT a[2] = {AT(0), AT(0)};
-        march<WI, K, D3>(ph, ne, ny, nz, a);
-        acc[0] = (double)a[0];
-        acc[1] = 0.0;
+        ph.f.src = (const S *)P.z; ph.f.scale = gamma; ph.t = (S *)P.r; ph.st = ct;
+        acc[0] = acc[1] = AT(0);
+        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
     }
-    __device__ void s1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2]) const
+    __device__ void s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
         PhS1<PREC, WI, K, D3> ph;
-        ph.src = (const S *)P.r; ph.pold = pold; ph.beta = beta; ph.first = first;
+        ph.f.src = (const S *)P.r; ph.f.pold = pold; ph.f.beta = beta; ph.f.first = first;
         ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs;
-        AT a[2] = {AT(0), AT(0)};
-        march<WI, K, D3>(ph, ne, ny, nz, a);
-        acc[0] = (double)a[0];
-        acc[1] = 0.0;
+        acc[0] = acc[1] = AT(0);
+        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
     }
-    __device__ void s2(bool first, C a_, const S *p, double (&acc)[2]) const
+    __device__ void s2(bool first, C a_, const S *p, AT (&acc)[2]) const
     {
         PhS2<PREC, WI, K, D3> ph;
-        ph.src = (const S *)P.u; ph.scale = C(1); ph.p = p; ph.y = (S *)P.y; ph.t = (S *)P.r;
+        ph.f.src = (const S *)P.u; ph.f.scale = C(1); ph.p = p; ph.y = (S *)P.y; ph.t = (S *)P.r;
         ph.a = a_; ph.first = first; ph.st = ct;
-        AT a[2] = {AT(0), AT(0)};
-        march<WI, K, D3>(ph, ne, ny, nz, a);
-        acc[0] = (double)a[0];
-        acc[1] = 0.0;
+        acc[0] = acc[1] = AT(0);
+        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
     }
     // complex class: S = (alpha + i sigma) I, y = fl_s(g / (alpha + i sigma))
     __device__ void s_pointwise(C gamma) const
@@ -561,7 +672,6 @@ struct StencilImpl {
             }
         }
     }
-    __device__ bool csr_pre_sync() const { return false; }
 };
 
 } // namespace gadi

@@ -9,7 +9,7 @@ namespace gadi {
 // elementwise helpers shared by all classes
 // ---------------------------------------------------------------------------
 template <int PREC>
-__device__ void phase_norm2(const void *v, long long m, double (&acc)[2])
+__device__ void phase_norm2(const void *v, long long m, typename AccT<PREC>::T (&acc)[2])
 {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -21,8 +21,8 @@ __device__ void phase_norm2(const void *v, long long m, double (&acc)[2])
         const AT x = (AT)PT::ld(s[i]);
         a += x * x;
     }
-    acc[0] = (double)a;
-    acc[1] = 0.0;
+    acc[0] = a;
+    acc[1] = AT(0);
 }
 
 template <int PREC>
@@ -77,7 +77,7 @@ struct CsrImpl {
         double a0 = 0.0, a1 = 0.0;
         S *rs = (S *)P.r;
         for (long long i = i0(); i < n; i += di()) {
-            const double ax = spmv_row<double, double, ArExact<double>>(P.rowptr, P.col, P.aval, xout, (int)i);
+            const double ax = spmv_row<double, double, ArFusedD>(P.rowptr, P.col, P.aval, xout, (int)i);
             const double r = __dsub_rn(P.b[i], ax);
             a0 = fma(r, r, a0);
             const S sv = PT::from_f64(r);
@@ -95,10 +95,10 @@ struct CsrImpl {
         // op selection is done on the host by pointing rowptr/col/aval at
         // the operator to apply
         for (long long i = i0(); i < n; i += di())
-            yout[i] = spmv_row<double, double, ArExact<double>>(P.rowptr, P.col, P.aval, x, (int)i);
+            yout[i] = spmv_row<double, double, ArFusedD>(P.rowptr, P.col, P.aval, x, (int)i);
         return true;
     }
-    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &gs) const
+    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &gs) const
     {
         const S *r = (const S *)P.r;
         for (long long i = i0(); i < n; i += di()) {
@@ -117,11 +117,11 @@ struct CsrImpl {
             q[i] = s;
             a += (AT)PT::ld(pnew[i]) * (AT)s;
         }
-        acc[0] = (double)a;
-        acc[1] = 0.0;
+        acc[0] = a;
+        acc[1] = AT(0);
         return true;
     }
-    __device__ bool h2(bool first, C a_, const S *p, double (&acc)[2], const GridSync &) const
+    __device__ bool h2(bool first, C a_, const S *p, AT (&acc)[2], const GridSync &) const
     {
         S *z = (S *)P.z, *r = (S *)P.r;
         const C *q = (const C *)P.q;
@@ -134,11 +134,11 @@ struct CsrImpl {
             const AT rr = (AT)PT::ld(rn);
             a += rr * rr;
         }
-        acc[0] = (double)a;
-        acc[1] = 0.0;
+        acc[0] = a;
+        acc[1] = AT(0);
         return true;
     }
-    __device__ bool s0(C gamma, double (&acc)[2], const GridSync &gs) const
+    __device__ bool s0(C gamma, AT (&acc)[2], const GridSync &gs) const
     {
         const S *z = (const S *)P.z;
         S *g = (S *)P.u;
@@ -156,11 +156,11 @@ struct CsrImpl {
             const AT x = (AT)PT::ld(ts);
             a += x * x;
         }
-        acc[0] = (double)a;
-        acc[1] = 0.0;
+        acc[0] = a;
+        acc[1] = AT(0);
         return true;
     }
-    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &gs) const
+    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &gs) const
     {
         const S *t = (const S *)P.r;
         for (long long i = i0(); i < n; i += di()) {
@@ -181,11 +181,11 @@ struct CsrImpl {
             const AT x = (AT)PT::ld(us);
             a += x * x;
         }
-        acc[0] = (double)a;
-        acc[1] = 0.0;
+        acc[0] = a;
+        acc[1] = AT(0);
         return true;
     }
-    __device__ bool s2(bool first, C a_, const S *p, double (&acc)[2], const GridSync &) const
+    __device__ bool s2(bool first, C a_, const S *p, AT (&acc)[2], const GridSync &) const
     {
         const S *u = (const S *)P.u;
         const S *tv = (const S *)P.tval;
@@ -202,8 +202,8 @@ struct CsrImpl {
             const AT x = (AT)PT::ld(tn);
             a += x * x;
         }
-        acc[0] = (double)a;
-        acc[1] = 0.0;
+        acc[0] = a;
+        acc[1] = AT(0);
         return true;
     }
     __device__ void s_pointwise(C) const {}
@@ -216,6 +216,7 @@ struct StencilAdapter {
     using S = typename SI::S;
     using C = typename SI::C;
     using A = typename SI::A;
+    using AT = typename SI::AT;
     static constexpr int K = SI::K;
     SI si;
     __device__ explicit StencilAdapter(const Params &p) : si(p) {}
@@ -230,27 +231,27 @@ struct StencilAdapter {
         si.apply(x, yout);
         return true;
     }
-    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &) const
+    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &) const
     {
         si.h1(first, beta, pold, pnew, acc);
         return true;
     }
-    __device__ bool h2(bool first, C a, const S *p, double (&acc)[2], const GridSync &) const
+    __device__ bool h2(bool first, C a, const S *p, AT (&acc)[2], const GridSync &) const
     {
         si.h2(first, a, p, acc);
         return true;
     }
-    __device__ bool s0(C gamma, double (&acc)[2], const GridSync &) const
+    __device__ bool s0(C gamma, AT (&acc)[2], const GridSync &) const
     {
         si.s0(gamma, acc);
         return true;
     }
-    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, double (&acc)[2], const GridSync &) const
+    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &) const
     {
         si.s1(first, beta, pold, pnew, acc);
         return true;
     }
-    __device__ bool s2(bool first, C a, const S *p, double (&acc)[2], const GridSync &) const
+    __device__ bool s2(bool first, C a, const S *p, AT (&acc)[2], const GridSync &) const
     {
         si.s2(first, a, p, acc);
         return true;
@@ -261,17 +262,22 @@ struct StencilAdapter {
 // ---------------------------------------------------------------------------
 // the control loop
 // ---------------------------------------------------------------------------
+// largest value of type C not above x (so that c <= x in double is c <= floor_to(x) in C)
+template <class C> __device__ __forceinline__ C floor_to(double x);
+template <> __device__ __forceinline__ float floor_to<float>(double x) { return __double2float_rd(x); }
+template <> __device__ __forceinline__ double floor_to<double>(double x) { return x; }
+
 template <int PREC, class Impl>
 struct Runner {
     using PT = Prec<PREC>;
     using S = typename PT::S;
     using C = typename PT::C;
     using A = typename InnerAr<PREC>::T;
+    using AT = typename AccT<PREC>::T;
     const Params &P;
     const Impl &I;
     GridSync gs;
     int slot = 0;
-    double sums[2];
 
     __device__ Runner(const Params &p, const Impl &i) : P(p), I(i)
     {
@@ -280,40 +286,44 @@ struct Runner {
         gs.nblocks = gridDim.x;
     }
 
-    __device__ bool reduce(double (&acc)[2])
+    // grid-wide sums of two per-thread partials; every block gets the same
+    // totals.  Two slots alternate so a fast block cannot overwrite partials a
+    // slow block is still reading.
+    template <class RT>
+    __device__ bool reduce(const RT (&acc)[2], RT (&out)[2])
     {
         const int G = gridDim.x;
-        double *part = P.part + (size_t)slot * 2 * G;
-        block_partials_write<2>(acc, part, G);
+        RT *part = reinterpret_cast<RT *>(P.part + (size_t)slot * 2 * G);
+        block_partials_write<2, RT>(acc, part, G);
         if (!gs.sync()) return false;
-        grid_partials_sum<2>(part, G, sums);
+        grid_partials_sum<2, RT>(part, G, out);
         slot ^= 1;
         return true;
     }
 
-    // CG on H = alpha I + M (right-hand side already in P.r, ||rhs||^2 = rr0d).
+    // CG on H = alpha I + M (right-hand side already in P.r, ||rhs||^2 = rr0).
     // Returns iterations, or -1 if a barrier gave up.
-    __device__ int h_loop(double rr0d)
+    __device__ int h_loop(C rr)
     {
         const long long m = P.nelem;
-        C rr = (C)rr0d;
         if (rr == C(0)) {
             phase_zero<PREC>(P.z, m);
             return gs.sync() ? 0 : -1;
         }
-        const double thr = P.tol_h * P.tol_h * (double)rr;
+        // stop when rn <= tol^2 rr0 (compared in double, evaluated in C)
+        const C thr = floor_to<C>(P.tol_h * P.tol_h * (double)rr);
         C beta = C(0), best = rr;
         int since = 0, its = 0;
-        double acc[2];
+        AT acc[2], sum[2];
         for (int j = 0; j < P.maxit_inner; ++j) {
             S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
             const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
-            if (!I.h1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc)) return -1;
-            const C a = A::div(rr, (C)sums[0]);
-            if (!I.h2(j == 0, a, pnew, acc, gs) || !reduce(acc)) return -1;
-            const C rn = (C)sums[0];
+            if (!I.h1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            const C a = A::div(rr, (C)sum[0]);
+            if (!I.h2(j == 0, a, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            const C rn = (C)sum[0];
             its = j + 1;
-            if ((double)rn <= thr) break;
+            if (rn <= thr) break;
             if (!(rn == rn)) break;
             if (rn < best) {
                 best = rn;
@@ -335,25 +345,25 @@ struct Runner {
             I.s_pointwise(gamma);
             return gs.sync() ? 1 : -1;
         }
-        double acc[2];
-        if (!I.s0(gamma, acc, gs) || !reduce(acc)) return -1;
-        C tt = (C)sums[0];
+        AT acc[2], sum[2];
+        if (!I.s0(gamma, acc, gs) || !reduce(acc, sum)) return -1;
+        C tt = (C)sum[0];
         if (tt == C(0)) {
             phase_zero<PREC>(P.y, m);
             return gs.sync() ? 0 : -1;
         }
-        const double thr = P.tol_s * P.tol_s * (double)tt;
+        const C thr = floor_to<C>(P.tol_s * P.tol_s * (double)tt);
         C beta = C(0), best = tt;
         int since = 0, its = 0;
         for (int j = 0; j < P.maxit_inner; ++j) {
             S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
             const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
-            if (!I.s1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc)) return -1;
-            const C a = A::div(tt, (C)sums[0]);
-            if (!I.s2(j == 0, a, pnew, acc, gs) || !reduce(acc)) return -1;
-            const C tn = (C)sums[0];
+            if (!I.s1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            const C a = A::div(tt, (C)sum[0]);
+            if (!I.s2(j == 0, a, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            const C tn = (C)sum[0];
             its = j + 1;
-            if ((double)tn <= thr) break;
+            if (tn <= thr) break;
             if (!(tn == tn)) break;
             if (tn < best) {
                 best = tn;
@@ -370,23 +380,24 @@ struct Runner {
     __device__ void run()
     {
         const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-        double acc[2];
+        double dacc[2], dsum[2];
         if (P.mode == MODE_APPLY) {
             I.apply(P.ax_in, P.ax_out, gs);
             return;
         }
         if (P.mode == MODE_RESIDUAL) {
-            if (!I.residual(P.x, (const S *)P.y, P.x1, acc, gs) || !reduce(acc)) return;
+            if (!I.residual(P.x, (const S *)P.y, P.x1, dacc, gs) || !reduce(dacc, dsum)) return;
             if (leader) {
-                P.ctl->rnorm = sqrt(sums[0]);
+                P.ctl->rnorm = sqrt(dsum[0]);
                 P.ctl->status = ST_OK;
             }
             return;
         }
         if (P.mode == MODE_SOLVE_H) {
+            AT acc[2], sum[2];
             phase_norm2<PREC>(P.r, P.nelem, acc);
-            if (!reduce(acc)) return;
-            const int its = h_loop(sums[0]);
+            if (!reduce(acc, sum)) return;
+            const int its = h_loop((C)sum[0]);
             if (leader && its >= 0) {
                 P.ctl->inner_h = its;
                 P.ctl->status = ST_OK;
@@ -409,9 +420,9 @@ struct Runner {
         for (k = 0;; ++k) {
             const double *xin = xb ? P.x1 : P.x;
             double *xout = xb ? P.x : P.x1;
-            if (!I.residual(xin, k > 0 ? (const S *)P.y : nullptr, xout, acc, gs) || !reduce(acc)) return;
+            if (!I.residual(xin, k > 0 ? (const S *)P.y : nullptr, xout, dacc, gs) || !reduce(dacc, dsum)) return;
             xb ^= 1;
-            const double rn = sqrt(sums[0]);
+            const double rn = sqrt(dsum[0]);
             if (k == 0) r0 = rn;
             rel = r0 > 0.0 ? rn / r0 : 0.0;
             if (leader) P.hist[k] = rel;
@@ -431,7 +442,7 @@ struct Runner {
                 status = ST_NOT_CONVERGED;
                 break;
             }
-            const int a = h_loop(sums[1]);
+            const int a = h_loop((C)dsum[1]);
             if (a < 0) return;
             ih += a;
             const int b = s_loop(gamma);
@@ -451,7 +462,7 @@ struct Runner {
 };
 
 template <int KIND, int PREC, int WI, int WR>
-__global__ void __launch_bounds__(kThreads) gadi_stencil_kernel(const __grid_constant__ Params P)
+__global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
     StencilAdapter<StencilImpl<KIND, PREC, WI, WR>> I(P);
     Runner<PREC, StencilAdapter<StencilImpl<KIND, PREC, WI, WR>>> R(P, I);
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) gadi_stencil_kernel(const __grid_con
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads) gadi_csr_kernel(const __grid_constant__ Params P)
+__global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_csr_kernel(const __grid_constant__ Params P)
 {
     CsrImpl<PREC> I(P);
     Runner<PREC, CsrImpl<PREC>> R(P, I);
