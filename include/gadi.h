@@ -201,6 +201,35 @@ gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_p
                               const void *z, void *y, double tol, int maxit, int stag,
                               int pointwise, int *its, void *stream);
 
+/* ---- allocation-free variant -------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc (code running inside a pre-sized memory pool,
+ * a host application that owns every device allocation, or a process that
+ * must not grow its device footprint once started).
+ *
+ * gadi_solve_h_2d_noalloc: the H-solve of the 2D 5-point class -- CG on
+ * (alpha I + M) z = rs with M the h^2-scaled 5-point Laplacian (centre 4,
+ * neighbours -1) on an nx x ny grid, from z = 0, with the stopping rules of
+ * gadi_step_solve_h -- computed by the same kernel and arithmetic as
+ * gadi_step_solve_h, but with no handle and no device allocation.  rs (read)
+ * and z (written) are DEVICE u_s vectors of nx*ny elements (double, float or
+ * BF16 bits); *its receives the iteration count.
+ *   - Scratch: a file-scope device array of about 10.6 MB that every GPU
+ *     loading the library holds until exit; the call makes no cudaMalloc,
+ *     cudaFree or other allocating call.
+ *   - Limit: nx*ny <= 262144 (for example 512 x 512); larger grids are
+ *     rejected with GADI_ERR_INVALID and a message in gadi_last_error().
+ *   - The first call on each device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one scratch array and leaves its contents
+ *     behind (the call clears what must start at zero).  Calls that overlap
+ *     on the GPU -- on different streams or host threads -- race on it and
+ *     must be serialised by the caller.
+ * Errors: INVALID, TIMEOUT, CUDA. */
+gadi_status gadi_solve_h_2d_noalloc(int nx, int ny, double alpha, gadi_prec u_low, const void *rs, void *z,
+                                    double tol, int maxit, int stag, int *its, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,8 +90,11 @@ def lib():
                                             C.c_int, ip, vp]
             L.gadi_step_solve_s.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp,
                                             C.c_double, C.c_int, C.c_int, C.c_int, ip, vp]
+            L.gadi_solve_h_2d_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, vp, vp,
+                                                  C.c_double, C.c_int, C.c_int, ip, vp]
             for f in ("gadi_create", "gadi_solve", "gadi_apply", "gadi_norm2_estimate",
-                      "gadi_step_residual", "gadi_step_solve_h", "gadi_step_solve_s"):
+                      "gadi_step_residual", "gadi_step_solve_h", "gadi_step_solve_s",
+                      "gadi_solve_h_2d_noalloc"):
                 getattr(L, f).restype = C.c_int
             _L = L
     return _L
@@ -109,6 +112,8 @@ def _ptr(a):
     """Raw pointer of a torch tensor or NumPy array (None -> NULL)."""
     if a is None:
         return None
+    if isinstance(a, int):  # a raw address
+        return a
     if hasattr(a, "data_ptr"):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
@@ -245,6 +250,19 @@ class Gadi:
         if st != OK:
             raise GadiError(st, "gadi_step_solve_s")
         return its.value
+
+
+def solve_h_2d_noalloc(nx, ny, alpha, u_low, rs, z, tol, maxit, stag=0, stream=None, check=True):
+    """gadi_solve_h_2d_noalloc: CG on (alpha I + M) z = rs for the 2D 5-point
+    class without any device allocation (for callers that cannot allocate;
+    the scratch is a static device array, grids up to 262144 points).
+    rs and z are device tensors in u_s.  Returns (status, iterations)."""
+    its = C.c_int()
+    st = lib().gadi_solve_h_2d_noalloc(int(nx), int(ny), float(alpha), int(u_low), _ptr(rs), _ptr(z),
+                                       float(tol), int(maxit), int(stag), C.byref(its), _stream(stream))
+    if check and st != OK:
+        raise GadiError(st, "gadi_solve_h_2d_noalloc")
+    return st, its.value
 
 
 def header_functions(path: str = HEADER) -> list[str]:

@@ -506,6 +506,12 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
 
 const char *gadi_last_error(void) { return g_last_error; }
 
+} // extern "C"
+
+void gadi::record_error(const char *msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
+extern "C" {
+
 const char *gadi_status_str(gadi_status s)
 {
     switch (s) {

@@ -7,4 +7,6 @@ const void *kernel_2d5(int prec, int vec);
 const void *kernel_3d7(int prec, int vec);
 const void *kernel_c2d5(int prec, int vec);
 const void *kernel_csr(int prec);
+// record a message for gadi_last_error() on this thread
+void record_error(const char *msg);
 } // namespace gadi
