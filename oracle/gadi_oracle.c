@@ -21,8 +21,11 @@
  *   arithmetic.  Every stored inner vector element is rounded to u_s at each
  *   write: r_s, the CG vectors r, p, z, the CGNR vectors t, p, y, the scaled
  *   right-hand side g and the intermediate S p of CGNR.  The products H p and
- *   S^T (S p), consumed where they are formed, and all dot products are
- *   carried in the compute type (double for FP64, float otherwise).
+ *   S^T (S p), consumed where they are formed, are carried in the compute
+ *   type (double for FP64, float otherwise).  An FP32 dot product is the
+ *   float nearest to the exact dot product of the stored vectors (the FP32
+ *   result a summation tree approaches; sequential FP32 accumulation would
+ *   add an order-dependent error of up to m u).
  *   FP32 arithmetic is C float arithmetic (IEEE binary32, round to nearest
  *   even; build with -ffp-contract=off so no fused multiply-add is formed).
  *   FP64 operator products are accumulated with C99 fma() (one rounding per
@@ -420,11 +423,15 @@ static double dot_d(int m, const double *a, const double *b)
     for (int i = 0; i < m; i++) s = s + a[i] * b[i];
     return s;
 }
+/* FP32 dot product of stored FP32 vectors: the FP32 value nearest to the
+ * exact dot product (products of floats are exact in double; the double sum
+ * carries 29 more bits than the float result).  Order-independent, unlike
+ * sequential FP32 accumulation, whose error grows with m. */
 static float dot_f(int m, const float *a, const float *b)
 {
-    float s = 0.0f;
-    for (int i = 0; i < m; i++) s = s + a[i] * b[i];
-    return s;
+    double s = 0.0;
+    for (int i = 0; i < m; i++) s = s + (double)a[i] * (double)b[i];
+    return (float)s;
 }
 
 /* CG on an SPD operator Op (H, or S^T S given as the pair S, St), double. */

@@ -195,7 +195,16 @@ def test_solve_s_converged(case, prec):
     tol = 1e-2 if prec == BF16 else 1e-4
     alpha, omega = 0.02, 1.0
     yg, it_g, yo, it_o = _solve_s_pair(p, prec, alpha, omega, z, tol, 1000, 10, False)
-    assert abs(it_g - it_o) <= max(2, 0.2 * it_o), (it_g, it_o)
+    # Iteration counts are comparable only where the tolerance is attainable in
+    # u_s (kappa(S^T S) u_s well below tol); beyond it both sides stop on the
+    # stagnation rule at a rounding-dependent step and only the result matters.
+    attainable = True
+    if p.kind != 3:
+        _, ks = G.condition_numbers(p, alpha)
+        u = {FP64: 1.11e-16, FP32: 5.96e-8, BF16: 3.91e-3}[prec]
+        attainable = ks * ks * u <= tol / 10
+    if attainable:
+        assert abs(it_g - it_o) <= max(2, 0.2 * it_o), (it_g, it_o)
     orc = O.Oracle(p)
     gvec = (2 - omega) * alpha * z
 
