@@ -269,6 +269,72 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "status": G.status_str(st), **s}))
 
 
+# Other configurations: the same measurement, one JSON line per precision.
+# Not the default headline line (that is the 2048^2 default above).
+WORKLOADS = {
+    # name: (builder, precisions, alpha factor, omega, maxit, inner tol per precision)
+    "c1": ("conv-diff-2d 64x64, beta=(10,10), alpha=0.5, omega=1, maxit 500, plain FP64", ["fp64"]),
+    "c3": ("conv-diff-3d 512^3 (n=134217728), beta=(1,1,1)U[1,50] seed 3", ["bf16", "fp32", "fp64"]),
+    "c4": ("complex reaction-diffusion 4096^2 (n=16777216 complex), kappa~U[0,10], sigma~U[1,100] seed 4",
+           ["bf16", "fp32", "fp64"]),
+}
+
+
+def run_workload(args):
+    """Time-to-tolerance of one configuration for each precision (one solve
+    each after a capped warm-up), with the same roofline accounting as the
+    headline line.  Solves that need more than --maxit outer iterations end
+    with their status reported; --fp64-maxit caps the slow FP64 runs (the
+    line then reports the per-outer-iteration time, not a time to tolerance)."""
+    import torch
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import alpha_star, config1, config3, config4
+    B.build()
+    name = args.workload
+    desc, precs = WORKLOADS[name]
+    if name == "c1":
+        p, xt, c = config1()
+        alpha, omega, maxit = c["alpha"], c["omega"], c["maxit"]
+    elif name == "c3":
+        p, xt = config3(args.grid3)
+        alpha, omega, maxit = args.alpha_factor * alpha_star(p), OMEGA, args.maxit
+    else:
+        p, xt = config4(args.grid4)
+        alpha, omega, maxit = alpha_star(p), 1.0, args.maxit
+    H = G.Gadi.from_problem(p)
+    xtd = torch.from_numpy(xt).cuda()
+    b = torch.zeros_like(xtd)
+    H.apply(G.OP_A, xtd, b)
+    x = torch.zeros_like(b)
+    r = torch.zeros_like(b)
+    hbm, src = _peaks()
+    dbytes = 16 if p.kind == 2 else 8
+    for pn in precs:
+        prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[pn]
+        sbytes = {"fp64": 8, "fp32": 4, "bf16": 2}[pn] * (2 if p.kind == 2 else 1)
+        tin = 1e-2 if pn == "bf16" else TOL_INNER
+        mit = min(maxit, args.fp64_maxit) if pn == "fp64" and name != "c1" else maxit
+        x.zero_()
+        H.solve(b, x, alpha, omega, prec, TOL, min(3, mit), tol_h=tin, tol_s=tin)  # warm-up
+        x.zero_()
+        st, s = H.solve(b, x, alpha, omega, prec, TOL, mit, tol_h=tin, tol_s=tin)
+        H.apply(G.OP_A, x, r)
+        relres = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+        ab = algorithmic_bytes(p.npoints, s, sbytes, dbytes)
+        ach = ab / s["seconds"] / 1e9
+        print(json.dumps({
+            "metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
+            "workload": name, "config": {"workload": desc, "alpha": alpha, "omega": omega, "u_s": pn,
+                                          "tol_inner": tin, "maxit": mit},
+            "value": s["seconds"], "unit": "s", "status": G.status_str(st), "outer_its": s["outer_its"],
+            "inner_its_h": s["inner_its_h"], "inner_its_s": s["inner_its_s"], "relres": relres,
+            "ms_per_outer": 1e3 * s["seconds"] / max(1, s["outer_its"]),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "peak_source": src}}), flush=True)
+
+
 def cpu_baseline(p, xt, alpha, gpu_stats, outer):
     """The CPU oracle timed on a bounded sample: `outer` outer iterations of
     Algorithm 1 (FP64 outer, FP32 inner) on the full grid, scaled to the
@@ -334,9 +400,17 @@ def main():
     ap.add_argument("--ref-outer", type=int, default=2800)
     ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
                     help="run one solve capped at --maxit outer iterations (for ncu) and exit")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4"],
+                    help="c2 (default): the headline line; others: per-precision lines")
+    ap.add_argument("--grid3", type=int, default=512)
+    ap.add_argument("--grid4", type=int, default=4096)
+    ap.add_argument("--alpha-factor", type=float, default=ALPHA_FACTOR)
+    ap.add_argument("--fp64-maxit", type=int, default=20000)
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.workload != "c2" and args.impl == "ours":
+        run_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

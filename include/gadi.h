@@ -104,7 +104,7 @@ typedef struct {
 /* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2
  * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
- * per SM), hist = NULL. */
+ * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
     double tol_s;          /* inner CGNR tolerance on S (normal residual)   */
@@ -118,6 +118,10 @@ typedef struct {
     int max_blocks;        /* cap on persistent blocks (0 = automatic)      */
     double *hist;          /* optional HOST array of maxit+1 doubles: relres
                               per outer iteration                           */
+    int batch_group;       /* gadi_solve_batched: blocks per group (0 = 8)  */
+    int alpha_restarts;    /* Sec. 4.3 step 3: on STAGNATED or DIVERGED,
+                              double alpha and continue from the last finite
+                              iterate, up to this many times (0 = off)      */
 } gadi_opts;
 
 typedef struct {
@@ -129,6 +133,8 @@ typedef struct {
     double seconds;         /* device time of the solve (CUDA events)        */
     int status;             /* same as the return value                      */
     int blocks;             /* persistent blocks launched                    */
+    double alpha;           /* alpha of the last run (after any restarts)    */
+    int restarts;           /* alpha restarts taken (Sec. 4.3 step 3)        */
 } gadi_stats;
 
 typedef struct gadi_handle gadi_handle;
@@ -166,6 +172,48 @@ void gadi_destroy(gadi_handle *h);
 gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha, double omega,
                        gadi_prec u_high, gadi_prec u_low, double tol, int maxit,
                        const gadi_opts *opts, gadi_stats *stats);
+
+/* Many independent systems and right-hand sides in one persistent launch
+ * (Algorithm 1 for each).  hs[s] (s < nsys): handles of the 2D 5-point class
+ * (other classes: GADI_ERR_UNSUPPORTED); b[s], x[s]: DEVICE arrays of nrhs
+ * consecutive vectors of system s ([nrhs][n_s] doubles), x in/out as in
+ * gadi_solve; alpha[s]: that system's regularisation; omega, precisions, tol,
+ * maxit and opts are shared.  The grid is split into groups of
+ * opts->batch_group blocks (default 8); each group takes (system, rhs) units
+ * from a device-side queue, largest system first.  per_unit (nullable) gets
+ * nsys*nrhs entries in the order s*nrhs + j, with `seconds` the unit's own
+ * device time.  Returns GADI_OK if every unit converged, else the first
+ * non-OK unit status; errors as gadi_solve. */
+gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const double *const *b,
+                               double *const *x, const double *alpha, double omega, gadi_prec u_high,
+                               gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
+                               gadi_stats *per_unit);
+
+/* Sec. 4.3, step 2: condition numbers of H = alpha I + M and S = alpha I + N
+ * from closed forms, for the stencil classes (host only, no GPU work).
+ * M's spectrum is the sum of 1D Dirichlet Laplacian spectra (plus kappa for
+ * the complex class), so kappa(H) = (alpha + lmax) / (alpha + lmin) exactly.
+ * N is normal with eigenvalues i (sum_i 2 c_i cos(j pi h_i)) (i sigma for the
+ * complex class), so kappa(S) <= sqrt(alpha^2 + ||N||^2) / alpha, the value
+ * returned (an upper bound; equal when N is singular).  CSR: UNSUPPORTED (no
+ * cheap estimate; step 2 is then skipped, as Sec. 4.3 allows). */
+gadi_status gadi_condition_numbers(const gadi_problem *prob, double alpha, double *kappa_h, double *kappa_s);
+
+/* Sec. 4.3, steps 2-3: the smallest alpha_out = alpha0 * 2^k (k >= 0, k <= 60)
+ * with kappa(H) kappa(S) u_s < tau (eq. 4.1; tau = 0.01 in the paper), using
+ * gadi_condition_numbers and u_s from Table 1 (BF16 3.91e-3, FP32 5.96e-8,
+ * FP64 1.11e-16).  Errors: INVALID, UNSUPPORTED (CSR). */
+gadi_status gadi_select_alpha(const gadi_problem *prob, double alpha0, gadi_prec u_low, double tau,
+                              double *alpha_out);
+
+/* Check of the bounded grid barrier (no counterpart in the paper): launches a
+ * small cooperative kernel on `nblocks` blocks in which block 0 never arrives
+ * at the barrier, so every other block's wait runs out after timeout_ms; the
+ * blocks unwind and the call returns GADI_ERR_TIMEOUT with the device still
+ * usable.  It makes no memory access out of bounds and has no other effect.
+ * Errors: INVALID (nblocks < 2 or above the co-resident maximum, timeout_ms
+ * not in (0, 10000]), CUDA. */
+gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms);
 
 /* y = Op x in FP64 for Op in {A, M, N, A^T} (Sec. 3.1 splitting).  x and y
  * may be host or device memory; stream as in gadi_opts (NULL = default). */

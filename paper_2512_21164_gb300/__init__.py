@@ -46,13 +46,14 @@ class Opts(C.Structure):
     _fields_ = [("tol_h", C.c_double), ("tol_s", C.c_double), ("maxit_inner", C.c_int),
                 ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
                 ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
-                ("hist", C.c_void_p)]
+                ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("outer_its", C.c_int), ("inner_its_h", C.c_longlong),
                 ("inner_its_s", C.c_longlong), ("relres", C.c_double), ("r0_norm", C.c_double),
-                ("seconds", C.c_double), ("status", C.c_int), ("blocks", C.c_int)]
+                ("seconds", C.c_double), ("status", C.c_int), ("blocks", C.c_int),
+                ("alpha", C.c_double), ("restarts", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +91,16 @@ def lib():
                                             C.c_int, ip, vp]
             L.gadi_step_solve_s.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp,
                                             C.c_double, C.c_int, C.c_int, C.c_int, ip, vp]
+            L.gadi_solve_batched.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, C.c_double, C.c_int,
+                                             C.c_int, C.c_double, C.c_int, C.POINTER(Opts),
+                                             C.POINTER(Stats)]
+            L.gadi_solve_batched.restype = C.c_int
+            L.gadi_condition_numbers.argtypes = [C.POINTER(Problem), C.c_double, dp, dp]
+            L.gadi_condition_numbers.restype = C.c_int
+            L.gadi_select_alpha.argtypes = [C.POINTER(Problem), C.c_double, C.c_int, C.c_double, dp]
+            L.gadi_select_alpha.restype = C.c_int
+            L.gadi_selftest_barrier.argtypes = [C.c_int, C.c_double]
+            L.gadi_selftest_barrier.restype = C.c_int
             L.gadi_solve_h_2d_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, vp, vp,
                                                   C.c_double, C.c_int, C.c_int, ip, vp]
             for f in ("gadi_create", "gadi_solve", "gadi_apply", "gadi_norm2_estimate",
@@ -250,6 +261,62 @@ class Gadi:
         if st != OK:
             raise GadiError(st, "gadi_step_solve_s")
         return its.value
+
+
+def selftest_barrier(nblocks=64, timeout_ms=50.0):
+    """gadi_selftest_barrier: a grid barrier whose wait runs out; returns the status
+    (GADI_ERR_TIMEOUT expected)."""
+    return lib().gadi_selftest_barrier(int(nblocks), float(timeout_ms))
+
+
+def _problem_struct(p):
+    P = Problem()
+    P.kind, P.nx, P.ny, P.nz, P.h = int(p.kind), int(p.nx), int(p.ny), int(p.nz), float(p.h)
+    P.beta = (C.c_double * 3)(*[float(x) for x in p.beta])
+    P.kappa, P.sigma = float(p.kappa), float(p.sigma)
+    return P
+
+
+def condition_numbers(p, alpha):
+    """gadi_condition_numbers (Sec. 4.3 step 2) for a workloads.Problem: (kappa_H, kappa_S bound)."""
+    kh, ks = C.c_double(), C.c_double()
+    st = lib().gadi_condition_numbers(C.byref(_problem_struct(p)), float(alpha), C.byref(kh), C.byref(ks))
+    if st != OK:
+        raise GadiError(st, "gadi_condition_numbers")
+    return kh.value, ks.value
+
+
+def select_alpha(p, alpha0, u_low, tau=0.01):
+    """gadi_select_alpha (Sec. 4.3 steps 2-3)."""
+    out = C.c_double()
+    st = lib().gadi_select_alpha(C.byref(_problem_struct(p)), float(alpha0), int(u_low), float(tau),
+                                 C.byref(out))
+    if st != OK:
+        raise GadiError(st, "gadi_select_alpha")
+    return out.value
+
+
+def solve_batched(systems, nrhs, bs, xs, alphas, omega=1.0, u_low=FP32, tol=1e-10, maxit=1000,
+                  opts=None, stream=None, check=True, **kw):
+    """gadi_solve_batched: `systems` are Gadi handles of the 2D 5-point class;
+    bs[s] / xs[s] are device tensors holding nrhs consecutive vectors of system s
+    (x in/out); alphas[s] per system.  Returns (status, list of per-unit stats
+    dicts in the order s*nrhs + j)."""
+    n = len(systems)
+    o = default_opts(u_low) if opts is None else opts
+    for k, v in kw.items():
+        setattr(o, k, v)
+    o.stream = _stream(stream)
+    H = (C.c_void_p * n)(*[h.h.value for h in systems])
+    B = (C.c_void_p * n)(*[_ptr(t) for t in bs])
+    X = (C.c_void_p * n)(*[_ptr(t) for t in xs])
+    A = (C.c_double * n)(*[float(a) for a in alphas])
+    S = (Stats * (n * nrhs))()
+    st = lib().gadi_solve_batched(H, n, int(nrhs), B, X, A, float(omega), FP64, int(u_low), float(tol),
+                                  int(maxit), C.byref(o), S)
+    if check and st < 0:
+        raise GadiError(st, "gadi_solve_batched")
+    return st, [S[i].as_dict() for i in range(n * nrhs)]
 
 
 def solve_h_2d_noalloc(nx, ny, alpha, u_low, rs, z, tol, maxit, stag=0, stream=None, check=True):

@@ -5,6 +5,7 @@
 #include "gadi.h"
 #include "gadi_inst.h"
 #include "gadi_params.h"
+#include "gadi_common.cuh"
 
 #include <cuda_runtime.h>
 
@@ -278,14 +279,22 @@ bool params_aligned(const Params &P)
     return true;
 }
 
-const void *pick_kernel(gadi_handle *h, int prec, bool aligned)
+const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem)
 {
+    *smem = 0;
     if (h->kind == GADI_CSR) return kernel_csr(prec);
     const long long ne = (long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1);
     const int vec = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
     const int v = aligned && (ne % vec) == 0;
-    if (h->kind == GADI_STENCIL_2D5) return kernel_2d5(prec, v);
-    if (h->kind == GADI_STENCIL_3D7) return kernel_3d7(prec, v);
+    if (h->kind == GADI_STENCIL_2D5) {
+        *smem = kernel_2d5_smem(prec, v);
+        return kernel_2d5(prec, v);
+    }
+    if (h->kind == GADI_STENCIL_3D7) {
+        *smem = kernel_3d7_smem(prec, v);
+        return kernel_3d7(prec, v);
+    }
+    *smem = kernel_c2d5_smem(prec, v);
     return kernel_c2d5(prec, v);
 }
 
@@ -301,10 +310,12 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     if (P.mode == MODE_APPLY && (!P.ax_in || !P.ax_out)) return GADI_ERR_INVALID;
     const bool al = params_aligned(P);
     if (!al && h->kind == GADI_COMPLEX_2D5) return GADI_ERR_INVALID; // complex vectors: 16-byte aligned
-    const void *k = pick_kernel(h, prec, al);
+    size_t smem = 0;
+    const void *k = pick_kernel(h, prec, al, &smem);
     if (!k) return GADI_ERR_UNSUPPORTED;
+    if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, smem));
     if (per_sm <= 0) return GADI_ERR_CUDA;
     int blocks = per_sm * h->nsm;
     if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
@@ -319,7 +330,7 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     CK(cudaMemsetAsync(h->d_abort, 0, 64, st));
     CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st));
     void *args[] = {&P};
-    CK(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreadsHost), args, 0, st));
+    CK(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreadsHost), args, smem, st));
     if (blocks_out) *blocks_out = blocks;
     return GADI_OK;
 }
@@ -396,6 +407,18 @@ __global__ void k_nonfinite(const double *v, long long n, int *flag)
             atomicExch(flag, 1);
             return;
         }
+}
+
+// block 0 never arrives: the other blocks' barrier waits run out
+__global__ void k_barrier_selftest(unsigned long long *counter, int *abort_flag, unsigned long long timeout_ns)
+{
+    if (blockIdx.x == 0) return;
+    GridSync gs;
+    gs.counter = counter;
+    gs.abort_flag = abort_flag;
+    gs.nblocks = gridDim.x;
+    gs.timeout_ns = timeout_ns;
+    (void)gs.sync();
 }
 
 gadi_status check_finite_dev(gadi_handle *h, const double *v, long long n, cudaStream_t st, bool *ok)
@@ -502,6 +525,8 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->stream = nullptr;
     o->max_blocks = 0;
     o->hist = nullptr;
+    o->batch_group = 0;
+    o->alpha_restarts = 0;
 }
 
 const char *gadi_last_error(void) { return g_last_error; }
@@ -555,7 +580,8 @@ gadi_status gadi_create(const gadi_problem *p, gadi_splitting split, gadi_handle
             h->nz = p->kind == GADI_STENCIL_3D7 ? p->nz : 1;
             h->npts = (long long)h->nx * h->ny * h->nz;
             h->nelem = h->kind == GADI_COMPLEX_2D5 ? 2 * h->npts : h->npts;
-            if ((long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1) > (1ll << 30)) st = GADI_ERR_INVALID;
+            // the kernels index work units and rows with 32-bit integers
+            if (h->nelem > (1ll << 31) - (1ll << 24)) st = GADI_ERR_INVALID;
             h->h = p->h > 0 ? p->h : 1.0 / (p->nx + 1);
             for (int k = 0; k < 3; k++) h->beta[k] = p->beta[k];
             h->kappa = p->kappa;
@@ -658,7 +684,10 @@ void gadi_destroy(gadi_handle *h)
     delete h;
 }
 
-gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha, double omega,
+} // extern "C"
+
+namespace {
+gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha, double omega,
                        gadi_prec u_high, gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
                        gadi_stats *stats)
 {
@@ -736,8 +765,282 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
         stats->seconds = ms * 1e-3;
         stats->status = c.status;
         stats->blocks = blocks;
+        stats->alpha = alpha;
+        stats->restarts = 0;
     }
     return (gadi_status)c.status;
+}
+
+// closed-form spectra of the stencil classes (Sec. 4.3 step 2)
+bool stencil_spectra(const gadi_problem *p, double *lmin, double *lmax, double *nnorm)
+{
+    if (!p || p->kind == GADI_CSR || p->kind < 0 || p->kind > GADI_CSR) return false;
+    if (p->nx <= 0 || p->ny <= 0 || (p->kind == GADI_STENCIL_3D7 && p->nz <= 0)) return false;
+    const double h = p->h > 0 ? p->h : 1.0 / (p->nx + 1);
+    const int dims = p->kind == GADI_STENCIL_3D7 ? 3 : 2;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    const double pi = 3.14159265358979323846;
+    double lo = 0, hi = 0, nn = 0;
+    for (int d = 0; d < dims; d++) {
+        const double t = pi / (2.0 * (n[d] + 1));
+        lo += 4.0 * std::sin(t) * std::sin(t); // 1D Dirichlet Laplacian 2 - 2 cos(j pi/(n+1))
+        hi += 4.0 * std::cos(t) * std::cos(t);
+        if (p->kind != GADI_COMPLEX_2D5) nn += 2.0 * std::fabs(p->beta[d] * h / 2.0) * std::cos(2.0 * t);
+    }
+    if (p->kind == GADI_COMPLEX_2D5) {
+        lo += p->kappa;
+        hi += p->kappa;
+        nn = std::fabs(p->sigma);
+    }
+    *lmin = lo;
+    *lmax = hi;
+    *nnorm = nn;
+    return true;
+}
+double unit_roundoff(int prec) { return prec == P_BF16 ? 3.91e-3 : (prec == P_FP32 ? 5.96e-8 : 1.11e-16); }
+} // namespace
+
+extern "C" {
+
+gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms)
+{
+    if (nblocks < 2 || !(timeout_ms > 0) || timeout_ms > 10000.0) return GADI_ERR_INVALID;
+    int dev = 0, nsm = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_barrier_selftest, 32, 0));
+    if (nblocks > per_sm * nsm) return GADI_ERR_INVALID;
+    unsigned long long *buf = nullptr;
+    CK(cudaMalloc(&buf, 128));
+    gadi_status st = GADI_OK;
+    int hab = 0;
+    unsigned long long *counter = buf;
+    int *abort_flag = (int *)(buf + 8);
+    unsigned long long tns = (unsigned long long)(timeout_ms * 1e6);
+    void *args[] = {&counter, &abort_flag, &tns};
+    cudaError_t e = cudaMemset(buf, 0, 128);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(nblocks), dim3(32), args, 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&hab, abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = cuda_err(e, "gadi_selftest_barrier", __LINE__);
+    else if (hab) st = GADI_ERR_TIMEOUT;
+    cudaFree(buf);
+    return st;
+}
+
+gadi_status gadi_condition_numbers(const gadi_problem *prob, double alpha, double *kappa_h, double *kappa_s)
+{
+    if (!prob || !kappa_h || !kappa_s || !(alpha > 0) || !std::isfinite(alpha)) return GADI_ERR_INVALID;
+    if (prob->kind == GADI_CSR) return GADI_ERR_UNSUPPORTED;
+    double lo, hi, nn;
+    if (!stencil_spectra(prob, &lo, &hi, &nn)) return GADI_ERR_INVALID;
+    *kappa_h = (alpha + hi) / (alpha + lo);
+    *kappa_s = std::sqrt(alpha * alpha + nn * nn) / alpha;
+    return GADI_OK;
+}
+
+gadi_status gadi_select_alpha(const gadi_problem *prob, double alpha0, gadi_prec u_low, double tau,
+                              double *alpha_out)
+{
+    if (!alpha_out || !(tau > 0)) return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    double a = alpha0;
+    for (int k = 0; k <= 60; k++, a *= 2.0) {
+        double kh, ks;
+        gadi_status st = gadi_condition_numbers(prob, a, &kh, &ks);
+        if (st != GADI_OK) return st;
+        if (kh * ks * unit_roundoff((int)u_low) < tau) {
+            *alpha_out = a;
+            return GADI_OK;
+        }
+    }
+    return GADI_ERR_INVALID;
+}
+
+gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha, double omega,
+                       gadi_prec u_high, gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
+                       gadi_stats *stats)
+{
+    gadi_opts o;
+    if (opts) o = *opts;
+    else gadi_opts_default(&o, u_low);
+    gadi_stats st1;
+    gadi_status s = solve_once(h, b, x, alpha, omega, u_high, u_low, tol, maxit, &o, &st1);
+    if (s < 0 || o.alpha_restarts <= 0 || (s != GADI_STAGNATED && s != GADI_DIVERGED)) {
+        if (stats) *stats = st1;
+        return s;
+    }
+    // Sec. 4.3 step 3: stop, increase alpha, repeat -- from the last iterate,
+    // with the tolerance kept relative to the first residual norm
+    gadi_stats acc = st1;
+    const double r0 = st1.r0_norm;
+    double a = alpha, rel = st1.relres;
+    int its_left = maxit - st1.outer_its;
+    for (int k = 0; k < o.alpha_restarts && (s == GADI_STAGNATED || s == GADI_DIVERGED) && its_left > 0; k++) {
+        a *= 2.0;
+        if (!(rel == rel) || std::isinf(rel)) return s; // no finite iterate to continue from
+        const double tol_k = r0 > 0 && rel > 0 ? tol / rel : tol;
+        gadi_opts ok = o;
+        ok.hist = nullptr;
+        gadi_stats sk;
+        s = solve_once(h, b, x, a, omega, u_high, u_low, tol_k, its_left, &ok, &sk);
+        if (s < 0) return s;
+        rel = rel * sk.relres;
+        its_left -= sk.outer_its;
+        acc.outer_its += sk.outer_its;
+        acc.inner_its_h += sk.inner_its_h;
+        acc.inner_its_s += sk.inner_its_s;
+        acc.seconds += sk.seconds;
+        acc.restarts = k + 1;
+        acc.alpha = a;
+        acc.status = s;
+    }
+    acc.relres = rel;
+    if (stats) *stats = acc;
+    return s;
+}
+
+gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const double *const *b,
+                               double *const *x, const double *alpha, double omega, gadi_prec u_high,
+                               gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
+                               gadi_stats *per_unit)
+{
+    if (!hs || !b || !x || !alpha || nsys <= 0 || nrhs <= 0) return GADI_ERR_INVALID;
+    if (!std::isfinite(omega) || std::isnan(tol)) return GADI_ERR_NONFINITE;
+    if (!(omega >= 0 && omega < 2) || u_high != GADI_FP64 || !(tol >= 0) || maxit < 0) return GADI_ERR_INVALID;
+    if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    gadi_opts o;
+    if (opts) o = *opts;
+    else gadi_opts_default(&o, u_low);
+    gadi_status s = opts_check(o);
+    if (s != GADI_OK) return s;
+    const int prec = (int)u_low;
+    const int vecw = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
+    bool vec = true;
+    long long max_n = 0;
+    for (int i = 0; i < nsys; i++) {
+        if (!hs[i] || !b[i] || !x[i]) return GADI_ERR_INVALID;
+        if (hs[i]->kind != GADI_STENCIL_2D5) return GADI_ERR_UNSUPPORTED;
+        if (!std::isfinite(alpha[i])) return GADI_ERR_NONFINITE;
+        if (!(alpha[i] > 0)) return GADI_ERR_INVALID;
+        if (!is_device_ptr(b[i]) || !is_device_ptr(x[i])) return GADI_ERR_INVALID;
+        if (hs[i]->nx % vecw || !aligned16(b[i]) || !aligned16(x[i]) || (hs[i]->nelem & 1)) vec = false;
+        max_n = std::max(max_n, hs[i]->nelem);
+    }
+    gadi_handle *h0 = hs[0];
+    cudaStream_t st = (cudaStream_t)o.stream;
+    size_t smem = 0;
+    const void *k = kernel_batched_2d5(prec, vec ? 1 : 0, &smem);
+    if (!k) return GADI_ERR_UNSUPPORTED;
+    if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, smem));
+    int total = per_sm * h0->nsm;
+    if (o.max_blocks > 0) total = std::min(total, o.max_blocks);
+    const int gsize = std::max(1, std::min(o.batch_group > 0 ? o.batch_group : 8, total));
+    const int ngroups = total / gsize;
+    if (ngroups <= 0) return GADI_ERR_INVALID;
+    const int nunits = nsys * nrhs;
+
+    // units, largest system first (stable)
+    std::vector<int> order(nunits);
+    for (int u = 0; u < nunits; u++) order[u] = u;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return hs[a / nrhs]->nelem > hs[c / nrhs]->nelem;
+    });
+    std::vector<Params> units(nunits);
+    for (int q = 0; q < nunits; q++) {
+        const int u = order[q], sy = u / nrhs, j = u % nrhs;
+        gadi_handle *h = hs[sy];
+        Params &P = units[q];
+        fill_base(h, P, prec);
+        fill_inner(h, P, prec, alpha[sy], omega);
+        P.mode = MODE_SOLVE;
+        P.b = b[sy] + (size_t)j * h->nelem;
+        P.x = x[sy] + (size_t)j * h->nelem;
+        P.tol = tol;
+        P.tol_h = o.tol_h;
+        P.tol_s = o.tol_s;
+        P.maxit = maxit;
+        P.maxit_inner = o.maxit_inner;
+        P.inner_stag = o.inner_stag;
+        P.outer_win = o.outer_stag_window;
+        P.pointwise = o.s_pointwise;
+    }
+    // device buffers for this call
+    const size_t slab = align256((size_t)max_n * elem_bytes(prec)), slab_d = align256((size_t)max_n * 8);
+    const size_t gwork = slab_d + 6 * slab;
+    const int hist_len = maxit + 2;
+    struct Buf {
+        void *p = nullptr;
+        ~Buf()
+        {
+            if (p) cudaFree(p);
+        }
+    } bu, bq, bw, bp, bb, bh, bc, bt;
+    CK(cudaMalloc(&bu.p, sizeof(Params) * (size_t)nunits));
+    CK(cudaMalloc(&bq.p, sizeof(int) * (2 + 32 * (size_t)ngroups)));
+    CK(cudaMalloc(&bw.p, gwork * (size_t)ngroups));
+    CK(cudaMalloc(&bp.p, sizeof(double) * 4 * (size_t)gsize * ngroups));
+    CK(cudaMalloc(&bb.p, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64));
+    CK(cudaMalloc(&bh.p, sizeof(double) * (size_t)hist_len * ngroups));
+    CK(cudaMalloc(&bc.p, sizeof(Ctl) * (size_t)nunits));
+    CK(cudaMalloc(&bt.p, sizeof(unsigned long long) * 2 * (size_t)nunits));
+    CK(cudaMemcpyAsync(bu.p, units.data(), sizeof(Params) * (size_t)nunits, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(bq.p, 0, sizeof(int) * (2 + 32 * (size_t)ngroups), st));
+    CK(cudaMemsetAsync(bb.p, 0, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64, st));
+    CK(cudaMemsetAsync(bc.p, 0, sizeof(Ctl) * (size_t)nunits, st));
+    BatchParams B;
+    std::memset(&B, 0, sizeof B);
+    B.units = (Params *)bu.p;
+    B.nunits = nunits;
+    B.gsize = gsize;
+    B.queue = (int *)bq.p;
+    B.group_unit = (int *)bq.p + 32;
+    B.work = (char *)bw.p;
+    B.group_work_bytes = gwork;
+    B.slab_bytes = slab;
+    B.slab_d_bytes = slab_d;
+    B.part = (double *)bp.p;
+    B.bar = (unsigned long long *)bb.p;
+    B.abort_flag = (int *)((unsigned long long *)bb.p + 8 * (size_t)ngroups);
+    B.hist = (double *)bh.p;
+    B.hist_len = hist_len;
+    B.ctl = (Ctl *)bc.p;
+    B.t0 = (unsigned long long *)bt.p;
+    B.t1 = B.t0 + nunits;
+    void *args[] = {&B};
+    CK(cudaEventRecord(h0->ev0, st));
+    CK(cudaLaunchCooperativeKernel(k, dim3(gsize * ngroups), dim3(kThreadsHost), args, smem, st));
+    CK(cudaEventRecord(h0->ev1, st));
+    std::vector<Ctl> hc(nunits);
+    std::vector<unsigned long long> ht(2 * (size_t)nunits);
+    int hab = 0;
+    CK(cudaMemcpyAsync(hc.data(), bc.p, sizeof(Ctl) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ht.data(), bt.p, sizeof(unsigned long long) * 2 * (size_t)nunits, cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaMemcpyAsync(&hab, B.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hab) return GADI_ERR_TIMEOUT;
+    gadi_status worst = GADI_OK;
+    for (int q = 0; q < nunits; q++) {
+        const int u = order[q];
+        const Ctl &c = hc[q];
+        if (c.status != GADI_OK && worst == GADI_OK) worst = (gadi_status)c.status;
+        if (per_unit) {
+            gadi_stats &S = per_unit[u];
+            S.outer_its = c.outer_its;
+            S.inner_its_h = c.inner_h;
+            S.inner_its_s = c.inner_s;
+            S.relres = c.relres;
+            S.r0_norm = c.r0;
+            S.seconds = (double)(ht[nunits + q] - ht[q]) * 1e-9;
+            S.status = c.status;
+            S.blocks = gsize;
+        }
+    }
+    return worst;
 }
 
 gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream)

@@ -120,6 +120,20 @@ template <class T, int W> struct VecIO {
 };
 
 // ---------------------------------------------------------------------------
+// the blocks working on one system: the whole grid for a single solve, a
+// group of blocks for one system of a batch
+// ---------------------------------------------------------------------------
+struct VGrid {
+    int b; // this block's index in the group
+    int n; // blocks in the group
+    __device__ long long tid() const { return (long long)b * blockDim.x + threadIdx.x; }
+    __device__ long long nthreads() const { return (long long)n * blockDim.x; }
+    __device__ long long warp() const { return (long long)b * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+    __device__ long long nwarps() const { return (long long)n * (blockDim.x >> 5); }
+};
+__device__ __forceinline__ VGrid whole_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+
+// ---------------------------------------------------------------------------
 // bounded grid barrier for the persistent cooperative kernel
 // ---------------------------------------------------------------------------
 // The launch is cooperative (all blocks co-resident), so the barrier always
@@ -149,6 +163,7 @@ struct GridSync {
     unsigned long long *counter; // zeroed before launch
     int *abort_flag;             // zeroed before launch; 1 = a wait timed out
     unsigned nblocks;
+    unsigned long long timeout_ns = kBarrierTimeoutNs;
 
     // returns false if this block must unwind (timeout here or elsewhere)
     __device__ bool sync() const
@@ -165,7 +180,7 @@ struct GridSync {
                 unsigned spins = 0;
                 while (ld_acquire_u64(counter) < target) {
                     if (ld_volatile_int(abort_flag)) { ok = 0; break; }
-                    if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
                         atomicExch(abort_flag, 1);
                         ok = 0;
                         break;
@@ -185,14 +200,15 @@ struct GridSync {
 // deterministic reductions
 // ---------------------------------------------------------------------------
 // Each block reduces NV per-thread partial sums (type RT) in a fixed tree and
-// writes them to part[k * G + blockIdx.x].  After a grid barrier every block
+// writes them to part[k * G + bi] (bi = the block's index among the G blocks
+// that work on one system).  After a grid barrier every block
 // reads all G partials and sums them in the same fixed order, so every block
 // holds bitwise identical totals and takes identical control decisions.
 // RT is float for the FP32/BF16 inner solves (FP64 throughput on this GPU is
 // about 1/60 of FP32, so double arithmetic on every thread would dominate a
 // reduction) and double for FP64 sums (the outer residual norm, GADI-FP64).
 template <int NV, class RT>
-__device__ __forceinline__ void block_partials_write(const RT (&v)[NV], RT *part, int G)
+__device__ __forceinline__ void block_partials_write(const RT (&v)[NV], RT *part, int G, int bi)
 {
     __shared__ RT red[NV][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -210,7 +226,7 @@ __device__ __forceinline__ void block_partials_write(const RT (&v)[NV], RT *part
             RT s = lane < nw ? red[k][lane] : RT(0);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) __stcg(part + (size_t)k * G + blockIdx.x, s);
+            if (lane == 0) __stcg(part + (size_t)k * G + bi, s);
         }
     }
 }

@@ -1,5 +1,6 @@
 // Kernel lookup across the per-class translation units.
 #pragma once
+#include <cstddef>
 namespace gadi {
 // vec = 1 selects the 16-byte vector path (requires the row length in
 // elements to be a multiple of the elements per 16 bytes), 0 the narrow path.
@@ -7,6 +8,12 @@ const void *kernel_2d5(int prec, int vec);
 const void *kernel_3d7(int prec, int vec);
 const void *kernel_c2d5(int prec, int vec);
 const void *kernel_csr(int prec);
+// dynamic shared memory (bytes) the selected stencil kernel needs at launch
+size_t kernel_2d5_smem(int prec, int vec);
+size_t kernel_3d7_smem(int prec, int vec);
+size_t kernel_c2d5_smem(int prec, int vec);
+// the batched persistent kernel for the 2D 5-point class
+const void *kernel_batched_2d5(int prec, int vec, size_t *smem);
 // record a message for gadi_last_error() on this thread
 void record_error(const char *msg);
 } // namespace gadi

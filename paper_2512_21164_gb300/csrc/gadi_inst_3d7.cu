@@ -18,4 +18,16 @@ const void *kernel_3d7(int prec, int vec)
     }
     return nullptr;
 }
+size_t kernel_3d7_smem(int prec, int vec)
+{
+    switch (prec) {
+    case P_FP64:
+        return vec ? StencilImpl<K_3D7, P_FP64, 2, 2>::DSMEM : StencilImpl<K_3D7, P_FP64, 1, 1>::DSMEM;
+    case P_FP32:
+        return vec ? StencilImpl<K_3D7, P_FP32, 4, 2>::DSMEM : StencilImpl<K_3D7, P_FP32, 1, 1>::DSMEM;
+    case P_BF16:
+        return vec ? StencilImpl<K_3D7, P_BF16, 8, 2>::DSMEM : StencilImpl<K_3D7, P_BF16, 1, 1>::DSMEM;
+    }
+    return 0;
+}
 } // namespace gadi

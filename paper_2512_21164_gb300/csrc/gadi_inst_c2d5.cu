@@ -18,4 +18,16 @@ const void *kernel_c2d5(int prec, int vec)
     }
     return nullptr;
 }
+size_t kernel_c2d5_smem(int prec, int vec)
+{
+    switch (prec) {
+    case P_FP64:
+        return StencilImpl<K_C2D5, P_FP64, 2, 2>::DSMEM;
+    case P_FP32:
+        return vec ? StencilImpl<K_C2D5, P_FP32, 4, 2>::DSMEM : StencilImpl<K_C2D5, P_FP32, 2, 2>::DSMEM;
+    case P_BF16:
+        return vec ? StencilImpl<K_C2D5, P_BF16, 8, 2>::DSMEM : StencilImpl<K_C2D5, P_BF16, 2, 2>::DSMEM;
+    }
+    return 0;
+}
 } // namespace gadi

@@ -25,6 +25,10 @@ constexpr int kThreads = 256;
 #ifndef GADI_MIN_BLOCKS
 #define GADI_MIN_BLOCKS 2
 #endif
+// 1: 2D inner phases stage rows through shared memory (march_smem)
+#ifndef GADI_SMEM_SWEEP
+#define GADI_SMEM_SWEEP 0
+#endif
 
 // ---------------------------------------------------------------------------
 // arithmetic policies
@@ -144,6 +148,18 @@ struct FieldDir {
         for (int v = 0; v < N; v++)
             o[v] = first ? PT::ld(r.s[v]) : PT::ld(PT::st(A::madd(beta, PT::ld(r.p[v]), PT::ld(r.s[v]))));
     }
+    // shared-memory staging (march_smem): field vector k, whether it is read
+    static constexpr int NF = 2;
+    __device__ const S *vec(int k) const { return k == 0 ? src : pold; }
+    __device__ bool used(int k) const { return k == 0 || !first; }
+    template <int N> __device__ void from_smem(const S *c0, const S *c1, Raw<N> &r) const
+    {
+#pragma unroll
+        for (int v = 0; v < N; v++) {
+            r.s[v] = c0[v];
+            r.p[v] = first ? S(0) : c1[v];
+        }
+    }
 };
 
 // a stored u_s vector, optionally scaled and re-rounded: fl_s(scale v)
@@ -167,6 +183,14 @@ struct FieldLoad {
             if constexpr (SCALE) o[v] = PT::ld(PT::st(A::mul(scale, PT::ld(r.s[v]))));
             else o[v] = PT::ld(r.s[v]);
         }
+    }
+    static constexpr int NF = 1;
+    __device__ const S *vec(int) const { return src; }
+    __device__ bool used(int) const { return true; }
+    template <int N> __device__ void from_smem(const S *c0, const S *, Raw<N> &r) const
+    {
+#pragma unroll
+        for (int v = 0; v < N; v++) r.s[v] = c0[v];
     }
 };
 
@@ -202,6 +226,18 @@ struct Slot {
     YNbr<typename F::template Raw<W>, D3> y;
 };
 
+// Balanced contiguous split of `nunits` work units over the warps of a
+// virtual grid, in 32-bit arithmetic (64-bit integer division is a long
+// instruction sequence; the host keeps nunits below 2^31).  Warp w gets
+// [w q + min(w, rem), ... + q + (w < rem)).
+__device__ __forceinline__ void split_units(int nunits, VGrid vg, int &u0, int &u1)
+{
+    const int GW = (int)vg.nwarps(), gw = (int)vg.warp();
+    const int q = nunits / GW, rem = nunits - q * GW;
+    u0 = gw * q + min(gw, rem);
+    u1 = u0 + q + (gw < rem ? 1 : 0);
+}
+
 // Load the raw data of row g into a slot.  Invalid rows (outside the grid)
 // get a zero field; halo raws are written only for the lanes that use them
 // (lane 0 / 31), own-point raws only for rows the warp outputs.
@@ -222,27 +258,24 @@ __device__ __forceinline__ void load_slot(const Ph &ph, Slot<Ph, W, K, D3> &sl, 
 }
 
 template <int W, int K, bool D3, int PD, class Ph, class AT>
-__device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2])
+__device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2], VGrid vg)
 {
     using FT = typename Ph::Fld::FT;
     using SL = Slot<Ph, W, K, D3>;
     const int lane = threadIdx.x & 31;
     const int nstrips = (ne + 32 * W - 1) / (32 * W);
     const int collen = D3 ? nz : ny;
-    const long long ncols = D3 ? (long long)nstrips * ny : (long long)nstrips;
+    const int ncols = D3 ? nstrips * ny : nstrips;
     const long long mstride = D3 ? (long long)ne * ny : (long long)ne;
-    const long long nunits = ncols * collen;
-    const long long GW = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    long long u = nunits * gw / GW;
-    const long long u1 = nunits * (gw + 1) / GW;
+    int u, u1;
+    split_units(ncols * collen, vg, u, u1);
     while (u < u1) {
-        const long long col = u / collen;
-        const int m0 = (int)(u - col * collen);
-        const int m1 = (int)min((long long)collen, (long long)m0 + (u1 - u));
+        const int col = u / collen;
+        const int m0 = u - col * collen;
+        const int m1 = min(collen, m0 + (u1 - u));
         u += m1 - m0;
-        const int strip = D3 ? (int)(col / ny) : (int)col;
-        const int yy = D3 ? (int)(col - (long long)strip * ny) : 0;
+        const int strip = D3 ? col / ny : col;
+        const int yy = D3 ? col - strip * ny : 0;
         const int e0 = strip * 32 * W + lane * W;
         const bool act = e0 < ne;
         const long long cbase = (D3 ? (long long)yy * ne : 0ll) + e0;
@@ -303,6 +336,161 @@ __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (
                 cu[v] = up[v];
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the shared-memory-staged sweep (2D and complex 2D, 16-byte rows per lane)
+// ---------------------------------------------------------------------------
+// Same work split and arithmetic as march(), but a row's inputs reach the SM
+// by asynchronous 16-byte copies (cp.async.cg) issued SMEM_PD rows ahead into
+// a per-warp ring of shared-memory slots, so the prefetch depth costs no
+// registers.  A slot holds, for every input vector of the phase, the 32
+// lanes' 16-byte chunks, plus the chunk left of the strip (copied by lane 0)
+// and right of it (lane 31) for each field vector.  Rows outside the grid and
+// chunks past the row ends are zero-filled by the copy itself (source size 0).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool fill)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = fill ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int SMEM_PD = 3;                         // rows copied ahead
+constexpr int SMEM_NS = SMEM_PD + 2;               // slots per warp
+constexpr int SMEM_SLOT = 4 * 32 * 16 + 4 * 16;    // <= 4 vectors, <= 2 field vectors
+constexpr int SMEM_WARP = SMEM_NS * SMEM_SLOT;
+
+// copy row m (element offset g of lane's chunk) of a phase into a slot
+template <int W, class Ph>
+__device__ __forceinline__ void smem_issue_row(const Ph &ph, unsigned char *slot, bool inrow, bool own, long long g,
+                                               int lane, int e0, int ne)
+{
+    using F = typename Ph::Fld;
+    using S = typename F::S;
+    constexpr int NF = F::NF, NO = Ph::NO, NV = NF + NO;
+    const bool act = e0 < ne;
+#pragma unroll
+    for (int k = 0; k < NF; k++) {
+        if (!ph.f.used(k)) continue;
+        const S *base = ph.f.vec(k);
+        const bool ok = inrow && act;
+        cp_async16(slot + k * 512 + lane * 16, ok ? (const void *)(base + g) : (const void *)base, ok);
+        if (lane == 0) {
+            const bool okl = inrow && act && e0 > 0;
+            cp_async16(slot + NV * 512 + k * 16, okl ? (const void *)(base + g - W) : (const void *)base, okl);
+        }
+        if (lane == 31) {
+            const bool okr = inrow && act && e0 + W < ne;
+            cp_async16(slot + NV * 512 + (NF + k) * 16, okr ? (const void *)(base + g + W) : (const void *)base,
+                       okr);
+        }
+    }
+    if (own) {
+#pragma unroll
+        for (int k = 0; k < NO; k++) {
+            if (!ph.own_used(k)) continue;
+            const S *base = ph.own_vec(k);
+            const bool ok = inrow && act;
+            cp_async16(slot + (NF + k) * 512 + lane * 16, ok ? (const void *)(base + g) : (const void *)base, ok);
+        }
+    }
+}
+
+template <int W, int K, class Ph, class AT>
+__device__ __forceinline__ void march_smem(const Ph &ph, int ne, int ny, AT (&acc)[2], unsigned char *wsm, VGrid vg)
+{
+    using F = typename Ph::Fld;
+    using S = typename F::S;
+    using FT = typename F::FT;
+    constexpr int NF = F::NF, NO = Ph::NO, NV = NF + NO;
+    static_assert(W * sizeof(S) == 16, "march_smem needs 16-byte lane chunks");
+    static_assert(NV <= 4 && NF <= 2, "slot layout");
+    const int lane = threadIdx.x & 31;
+    const int nstrips = (ne + 32 * W - 1) / (32 * W);
+    int u, u1;
+    split_units(nstrips * ny, vg, u, u1);
+    while (u < u1) {
+        const int strip = u / ny;
+        const int m0 = u - strip * ny;
+        const int m1 = min(ny, m0 + (u1 - u));
+        u += m1 - m0;
+        const int e0 = strip * 32 * W + lane * W;
+        const bool act = e0 < ne;
+        const long long cbase = e0;
+        // slot of row m: (m - m0 + 1) % SMEM_NS
+        auto slot_of = [&](int m) { return wsm + ((m - m0 + 1) % SMEM_NS) * SMEM_SLOT; };
+        for (int r = m0 - 1; r < m0 + SMEM_PD; ++r) {
+            smem_issue_row<W>(ph, slot_of(r), r >= 0 && r < ny, r >= m0 && r < m1, cbase + (long long)r * ne,
+                              lane, e0, ne);
+            cp_async_commit();
+        }
+        FT dn[W], cu[W], up[W];
+        for (int m = m0; m < m1; ++m) {
+            {
+                const int r = m + SMEM_PD;
+                smem_issue_row<W>(ph, slot_of(r), r < ny, r < m1, cbase + (long long)r * ne, lane, e0, ne);
+                cp_async_commit();
+            }
+            cp_async_wait<SMEM_PD - 1>(); // rows <= m + 1 have landed
+            __syncwarp();
+            typename F::template Raw<W> raw;
+            if (m == m0) {
+                const unsigned char *sd = slot_of(m0 - 1), *sc = slot_of(m0);
+                ph.f.template from_smem<W>((const S *)(sd + lane * 16), (const S *)(sd + 512 + lane * 16), raw);
+                ph.f.template value<W>(raw, dn);
+                ph.f.template from_smem<W>((const S *)(sc + lane * 16), (const S *)(sc + 512 + lane * 16), raw);
+                ph.f.template value<W>(raw, cu);
+            }
+            const unsigned char *sc = slot_of(m), *su = slot_of(m + 1);
+            ph.f.template from_smem<W>((const S *)(su + lane * 16), (const S *)(su + 512 + lane * 16), raw);
+            ph.f.template value<W>(raw, up);
+            FT lh[K], rh[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                lh[k] = __shfl_up_sync(0xffffffffu, cu[W - K + k], 1);
+                rh[k] = __shfl_down_sync(0xffffffffu, cu[k], 1);
+            }
+            if (lane == 0) {
+                typename F::template Raw<K> rk;
+                const unsigned char *h = sc + NV * 512;
+                ph.f.template from_smem<K>((const S *)h + (W - K), (const S *)(h + 16) + (W - K), rk);
+                ph.f.template value<K>(rk, lh);
+            }
+            if (lane == 31) {
+                typename F::template Raw<K> rk;
+                const unsigned char *h = sc + NV * 512 + NF * 16;
+                ph.f.template from_smem<K>((const S *)h, (const S *)(h + 16), rk);
+                ph.f.template value<K>(rk, rh);
+            }
+            FT w[W], e[W];
+#pragma unroll
+            for (int v = 0; v < W; v++) {
+                w[v] = (v >= K) ? cu[v - K] : lh[v];
+                e[v] = (v + K < W) ? cu[v + K] : rh[v + K - W];
+            }
+            if (act) {
+                typename Ph::Own o;
+                const S *oc[NO > 0 ? NO : 1];
+#pragma unroll
+                for (int k = 0; k < NO; k++) oc[k] = (const S *)(sc + (NF + k) * 512 + lane * 16);
+                ph.own_from_smem(oc, o);
+                ph.out(cbase + (long long)m * ne, o, cu, w, e, dn, up, dn, up, acc);
+            }
+            __syncwarp(); // every lane is done with row m's slot before it is refilled
+#pragma unroll
+            for (int v = 0; v < W; v++) {
+                dn[v] = cu[v];
+                cu[v] = up[v];
+            }
+        }
+        cp_async_wait<0>();
+        __syncwarp();
     }
 }
 
@@ -374,6 +562,10 @@ struct PhH1 {
     S *qout;
     Coef7<C> h;
     __device__ void load_own(long long, Own &) const {}
+    static constexpr int NO = 0;
+    __device__ const S *own_vec(int) const { return nullptr; }
+    __device__ bool own_used(int) const { return false; }
+    __device__ void own_from_smem(const S *const *, Own &) const {}
     template <class AT>
     __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
@@ -411,6 +603,17 @@ struct PhH2 {
         if (!first) VecIO<S, W>::load(z + g, o.v[0]);
         VecIO<S, W>::load(r + g, o.v[1]);
     }
+    static constexpr int NO = 2;
+    __device__ const S *own_vec(int k) const { return k == 0 ? z : r; }
+    __device__ bool own_used(int k) const { return k == 1 || !first; }
+    __device__ void own_from_smem(const S *const *c, Own &o) const
+    {
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+            o.v[0][v] = first ? S(0) : c[0][v];
+            o.v[1][v] = c[1][v];
+        }
+    }
     template <class AT>
     __device__ void out(long long g, const Own &o, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
@@ -443,6 +646,10 @@ struct PhS0 {
     S *t;
     Coef7<C> st;
     __device__ void load_own(long long, Own &) const {}
+    static constexpr int NO = 0;
+    __device__ const S *own_vec(int) const { return nullptr; }
+    __device__ bool own_used(int) const { return false; }
+    __device__ void own_from_smem(const S *const *, Own &) const {}
     template <class AT>
     __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
@@ -473,6 +680,10 @@ struct PhS1 {
     S *pnew, *u;
     Coef7<C> sc;
     __device__ void load_own(long long, Own &) const {}
+    static constexpr int NO = 0;
+    __device__ const S *own_vec(int) const { return nullptr; }
+    __device__ bool own_used(int) const { return false; }
+    __device__ void own_from_smem(const S *const *, Own &) const {}
     template <class AT>
     __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
@@ -513,6 +724,18 @@ struct PhS2 {
         if (!first) VecIO<S, W>::load(y + g, o.v[1]);
         VecIO<S, W>::load(t + g, o.v[2]);
     }
+    static constexpr int NO = 3;
+    __device__ const S *own_vec(int k) const { return k == 0 ? p : (k == 1 ? y : t); }
+    __device__ bool own_used(int k) const { return k != 1 || !first; }
+    __device__ void own_from_smem(const S *const *c, Own &o) const
+    {
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+            o.v[0][v] = c[0][v];
+            o.v[1][v] = first ? S(0) : c[1][v];
+            o.v[2][v] = c[2][v];
+        }
+    }
     template <class AT>
     __device__ void out(long long g, const Own &o, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&tt)[W], AT (&acc)[2]) const
@@ -546,13 +769,17 @@ struct StencilImpl {
     static constexpr int K = (KIND == K_C2D5) ? 2 : 1;
     static constexpr bool D3 = (KIND == K_3D7);
     static constexpr bool STORE_Q = (PREC == P_FP64);
-    static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead
+    static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead (register ring)
+    // 2D rows with 16-byte lane chunks go through the shared-memory-staged sweep
+    static constexpr bool USE_SMEM = GADI_SMEM_SWEEP && !D3 && (WI * sizeof(S) == 16);
+    static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : 0; // dynamic shared bytes
     const Params &P;
+    VGrid vg;
     int ne, ny, nz;
     Coef7<double> ca;
     Coef7<C> ch, cs, ct;
 
-    __device__ explicit StencilImpl(const Params &p) : P(p)
+    __device__ StencilImpl(const Params &p, VGrid g) : P(p), vg(g)
     {
         ne = p.nx * K;
         ny = p.ny;
@@ -570,11 +797,25 @@ struct StencilImpl {
         }
     }
 
+    __device__ static unsigned char *warp_smem()
+    {
+        extern __shared__ __align__(16) unsigned char gadi_dsmem[];
+        return gadi_dsmem + (threadIdx.x >> 5) * SMEM_WARP;
+    }
+    // run a phase over the grid with the sweep this instantiation uses
+    template <class Ph>
+    __device__ void sweep(const Ph &ph, AT (&acc)[2]) const
+    {
+        acc[0] = acc[1] = AT(0);
+        if constexpr (USE_SMEM) march_smem<WI, K>(ph, ne, ny, acc, warp_smem(), vg);
+        else march<WI, K, D3, PD>(ph, ne, ny, nz, acc, vg);
+    }
+
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
         PhResidual<PREC, WR, K, D3> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca};
         double a[2] = {0.0, 0.0};
-        march<WR, K, D3, PD>(ph, ne, ny, nz, a);
+        march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
         acc[1] = a[1];
     }
@@ -582,15 +823,14 @@ struct StencilImpl {
     {
         PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca};
         double a[2] = {0.0, 0.0};
-        march<WR, K, D3, PD>(ph, ne, ny, nz, a);
+        march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
     }
     __device__ void h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
         PhH1<PREC, WI, K, D3, STORE_Q> ph;
         ph.f.src = (const S *)P.r; ph.f.pold = pold; ph.f.beta = beta; ph.f.first = first;
         ph.pnew = pnew; ph.qout = (S *)P.u; ph.h = ch;
-        acc[0] = acc[1] = AT(0);
-        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+        sweep(ph, acc);
     }
     __device__ void h2(bool first, C a_, const S *p, AT (&acc)[2]) const
     {
@@ -601,8 +841,7 @@ struct StencilImpl {
             const S *q = (const S *)P.u;
             AT s = AT(0);
             const long long nv = P.nelem / WI;
-            for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
-                 i += (long long)gridDim.x * blockDim.x) {
+            for (long long i = vg.tid(); i < nv; i += vg.nthreads()) {
                 const long long g = i * WI;
                 S pv[WI], qv[WI], zv[WI], rv[WI];
                 V::load(p + g, pv);
@@ -624,32 +863,28 @@ struct StencilImpl {
             PhH2<PREC, WI, K, D3> ph;
             ph.f.src = p; ph.f.scale = C(1);
             ph.z = (S *)P.z; ph.r = (S *)P.r; ph.a = a_; ph.first = first; ph.h = ch;
-            acc[0] = acc[1] = AT(0);
-            march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+            sweep(ph, acc);
         }
     }
     __device__ void s0(C gamma, AT (&acc)[2]) const
     {
         PhS0<PREC, WI, K, D3> ph;
         ph.f.src = (const S *)P.z; ph.f.scale = gamma; ph.t = (S *)P.r; ph.st = ct;
-        acc[0] = acc[1] = AT(0);
-        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+        sweep(ph, acc);
     }
     __device__ void s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
         PhS1<PREC, WI, K, D3> ph;
         ph.f.src = (const S *)P.r; ph.f.pold = pold; ph.f.beta = beta; ph.f.first = first;
         ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs;
-        acc[0] = acc[1] = AT(0);
-        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+        sweep(ph, acc);
     }
     __device__ void s2(bool first, C a_, const S *p, AT (&acc)[2]) const
     {
         PhS2<PREC, WI, K, D3> ph;
         ph.f.src = (const S *)P.u; ph.f.scale = C(1); ph.p = p; ph.y = (S *)P.y; ph.t = (S *)P.r;
         ph.a = a_; ph.first = first; ph.st = ct;
-        acc[0] = acc[1] = AT(0);
-        march<WI, K, D3, PD>(ph, ne, ny, nz, acc);
+        sweep(ph, acc);
     }
     // complex class: S = (alpha + i sigma) I, y = fl_s(g / (alpha + i sigma))
     __device__ void s_pointwise(C gamma) const
@@ -661,8 +896,7 @@ struct StencilImpl {
             const S *z = (const S *)P.z;
             S *y = (S *)P.y;
             const long long np = (long long)P.nx * ny;
-            for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
-                 i += (long long)gridDim.x * blockDim.x) {
+            for (long long i = vg.tid(); i < np; i += vg.nthreads()) {
                 const C gr = PT::ld(PT::st(A::mul(gamma, PT::ld(z[2 * i]))));
                 const C gi = PT::ld(PT::st(A::mul(gamma, PT::ld(z[2 * i + 1]))));
                 const C yr = AE::div(AE::add(AE::mul(gr, ar), AE::mul(gi, ai)), den);

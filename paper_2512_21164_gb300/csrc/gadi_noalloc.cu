@@ -131,7 +131,11 @@ extern "C" gadi_status gadi_solve_h_2d_noalloc(int nx, int ny, double alpha, gad
     const int vec_elems = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
     const bool vec = (nx % vec_elems) == 0 && ((uintptr_t)z & 15u) == 0;
     const void *kern = kernel_2d5(prec, vec ? 1 : 0);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsNA, 0)) != cudaSuccess)
+    const size_t smem = kernel_2d5_smem(prec, vec ? 1 : 0);
+    if (smem && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                    cudaSuccess)
+        return na_fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreadsNA, smem)) != cudaSuccess)
         return na_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     int blocks = per_sm * nsm;
     if (blocks > kNoAllocMaxBlocks) blocks = kNoAllocMaxBlocks;
@@ -171,7 +175,7 @@ extern "C" gadi_status gadi_solve_h_2d_noalloc(int nx, int ny, double alpha, gad
     if ((e = cudaMemcpyAsync(slab[0], rs, eb * (size_t)n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return na_fail(e, "cudaMemcpyAsync");
     void *args[] = {&P};
-    if ((e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kThreadsNA), args, 0, st)) != cudaSuccess)
+    if ((e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kThreadsNA), args, smem, st)) != cudaSuccess)
         return na_fail(e, "cudaLaunchCooperativeKernel");
     Ctl hc;
     int hab = 0;

@@ -65,4 +65,23 @@ struct Params {
     int *abort_flag;
 };
 
+// One batched launch: units (system, right-hand side) taken from a queue by
+// groups of `gsize` blocks.  Per-group state is strided by group index.
+struct BatchParams {
+    Params *units;  // device array, one per unit; the group leader patches the work pointers
+    int nunits;
+    int gsize;      // blocks per group
+    int *queue;     // next unit to take (zeroed before launch)
+    int *group_unit; // per group (stride 32 ints): the unit it is working on
+    // per-group work: x1 (FP64) and six u_s vectors, each slab_bytes long
+    char *work;
+    size_t group_work_bytes, slab_bytes, slab_d_bytes;
+    double *part;   // per group 4 * gsize doubles
+    unsigned long long *bar; // per group barrier counter (stride 8)
+    double *hist;   // per group hist_len doubles
+    int hist_len;
+    Ctl *ctl;       // per unit
+    unsigned long long *t0, *t1; // per unit start / end (globaltimer ns)
+    int *abort_flag;
+};
 } // namespace gadi

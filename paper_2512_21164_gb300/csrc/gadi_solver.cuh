@@ -9,15 +9,14 @@ namespace gadi {
 // elementwise helpers shared by all classes
 // ---------------------------------------------------------------------------
 template <int PREC>
-__device__ void phase_norm2(const void *v, long long m, typename AccT<PREC>::T (&acc)[2])
+__device__ void phase_norm2(const void *v, long long m, typename AccT<PREC>::T (&acc)[2], VGrid vg)
 {
     using PT = Prec<PREC>;
     using S = typename PT::S;
     using AT = typename AccT<PREC>::T;
     const S *s = (const S *)v;
     AT a = AT(0);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = vg.tid(); i < m; i += vg.nthreads()) {
         const AT x = (AT)PT::ld(s[i]);
         a += x * x;
     }
@@ -26,13 +25,11 @@ __device__ void phase_norm2(const void *v, long long m, typename AccT<PREC>::T (
 }
 
 template <int PREC>
-__device__ void phase_zero(void *v, long long m)
+__device__ void phase_zero(void *v, long long m, VGrid vg)
 {
     using S = typename Prec<PREC>::S;
     S *s = (S *)v;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (long long)gridDim.x * blockDim.x)
-        s[i] = S(0);
+    for (long long i = vg.tid(); i < m; i += vg.nthreads()) s[i] = S(0);
 }
 
 // ---------------------------------------------------------------------------
@@ -49,11 +46,12 @@ struct CsrImpl {
     using AT = typename AccT<PREC>::T;
     static constexpr int K = 1;
     const Params &P;
+    VGrid vg;
     int n;
-    __device__ explicit CsrImpl(const Params &p) : P(p) { n = (int)p.npts; }
+    __device__ CsrImpl(const Params &p, VGrid g) : P(p), vg(g) { n = (int)p.npts; }
 
-    __device__ long long i0() const { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
-    __device__ long long di() const { return (long long)gridDim.x * blockDim.x; }
+    __device__ long long i0() const { return vg.tid(); }
+    __device__ long long di() const { return vg.nthreads(); }
 
     template <class VT, class XT, class AR>
     __device__ VT spmv_row(const int *rp, const int *cl, const VT *val, const XT *x, int i) const
@@ -219,7 +217,8 @@ struct StencilAdapter {
     using AT = typename SI::AT;
     static constexpr int K = SI::K;
     SI si;
-    __device__ explicit StencilAdapter(const Params &p) : si(p) {}
+    VGrid vg;
+    __device__ StencilAdapter(const Params &p, VGrid g) : si(p, g), vg(g) {}
     __device__ bool residual(const double *xin, const S *y, double *xout, double (&acc)[2],
                              const GridSync &) const
     {
@@ -283,7 +282,7 @@ struct Runner {
     {
         gs.counter = p.bar;
         gs.abort_flag = p.abort_flag;
-        gs.nblocks = gridDim.x;
+        gs.nblocks = (unsigned)i.vg.n;
     }
 
     // grid-wide sums of two per-thread partials; every block gets the same
@@ -292,9 +291,9 @@ struct Runner {
     template <class RT>
     __device__ bool reduce(const RT (&acc)[2], RT (&out)[2])
     {
-        const int G = gridDim.x;
+        const int G = I.vg.n;
         RT *part = reinterpret_cast<RT *>(P.part + (size_t)slot * 2 * G);
-        block_partials_write<2, RT>(acc, part, G);
+        block_partials_write<2, RT>(acc, part, G, I.vg.b);
         if (!gs.sync()) return false;
         grid_partials_sum<2, RT>(part, G, out);
         slot ^= 1;
@@ -307,7 +306,7 @@ struct Runner {
     {
         const long long m = P.nelem;
         if (rr == C(0)) {
-            phase_zero<PREC>(P.z, m);
+            phase_zero<PREC>(P.z, m, I.vg);
             return gs.sync() ? 0 : -1;
         }
         // stop when rn <= tol^2 rr0 (compared in double, evaluated in C)
@@ -349,7 +348,7 @@ struct Runner {
         if (!I.s0(gamma, acc, gs) || !reduce(acc, sum)) return -1;
         C tt = (C)sum[0];
         if (tt == C(0)) {
-            phase_zero<PREC>(P.y, m);
+            phase_zero<PREC>(P.y, m, I.vg);
             return gs.sync() ? 0 : -1;
         }
         const C thr = floor_to<C>(P.tol_s * P.tol_s * (double)tt);
@@ -379,7 +378,7 @@ struct Runner {
 
     __device__ void run()
     {
-        const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+        const bool leader = I.vg.b == 0 && threadIdx.x == 0;
         double dacc[2], dsum[2];
         if (P.mode == MODE_APPLY) {
             I.apply(P.ax_in, P.ax_out, gs);
@@ -395,7 +394,7 @@ struct Runner {
         }
         if (P.mode == MODE_SOLVE_H) {
             AT acc[2], sum[2];
-            phase_norm2<PREC>(P.r, P.nelem, acc);
+            phase_norm2<PREC>(P.r, P.nelem, acc, I.vg);
             if (!reduce(acc, sum)) return;
             const int its = h_loop((C)sum[0]);
             if (leader && its >= 0) {
@@ -464,7 +463,7 @@ struct Runner {
 template <int KIND, int PREC, int WI, int WR>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
-    StencilAdapter<StencilImpl<KIND, PREC, WI, WR>> I(P);
+    StencilAdapter<StencilImpl<KIND, PREC, WI, WR>> I(P, whole_grid());
     Runner<PREC, StencilAdapter<StencilImpl<KIND, PREC, WI, WR>>> R(P, I);
     R.run();
 }
@@ -472,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_csr_kernel(const __grid_constant__ Params P)
 {
-    CsrImpl<PREC> I(P);
+    CsrImpl<PREC> I(P, whole_grid());
     Runner<PREC, CsrImpl<PREC>> R(P, I);
     R.run();
 }

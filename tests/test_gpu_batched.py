@@ -1,0 +1,77 @@
+"""The batched persistent solve (many systems and right-hand sides in one
+launch) against the CPU oracle: every (system, right-hand side) unit must
+reach the oracle's outcome for that system, within the outer-iteration band
+of the single-system tests, and match the single-system GPU solve."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2512_21164_gb300 as G
+from helpers import BF16, FP32, FP64, dev64
+from workloads import SplitMix64, alpha_star, conv_diff_2d
+
+pytestmark = pytest.mark.gpu
+BAND = {FP64: 0.05, FP32: 0.10, BF16: 0.25}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2512_21164_gb300 import build
+    build.build()
+
+
+def _systems():
+    out = []
+    for i, (nx, ny) in enumerate([(32, 32), (24, 20), (16, 16), (40, 8)]):
+        p, _ = conv_diff_2d(nx, 400 + i, ny=ny)
+        out.append((p, 2.0 * alpha_star(p)))
+    return out
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+@pytest.mark.parametrize("group", [1, 4])
+def test_batched_matches_oracle(prec, group):
+    import torch
+    nrhs = 2
+    systems = _systems()
+    g = SplitMix64(77)
+    handles, bs, xs, alphas, rhs = [], [], [], [], []
+    for p, a in systems:
+        orc = O.Oracle(p)
+        bb = np.concatenate([orc.rhs(g.uniform_array(p.nvec)) for _ in range(nrhs)])
+        rhs.append(bb)
+        handles.append(G.Gadi.from_problem(p))
+        bs.append(dev64(bb))
+        xs.append(torch.zeros(nrhs * p.nvec, dtype=torch.float64, device="cuda"))
+        alphas.append(a)
+    tol_in = 1e-2 if prec == BF16 else 1e-3
+    st, stats = G.solve_batched(handles, nrhs, bs, xs, alphas, 1.0, prec, 1e-10, 3000,
+                                tol_h=tol_in, tol_s=tol_in, batch_group=group)
+    assert st == G.OK, G.status_str(st)
+    for s, (p, a) in enumerate(systems):
+        orc = O.Oracle(p)
+        xg_all = xs[s].cpu().numpy()
+        for j in range(nrhs):
+            b = rhs[s][j * p.nvec:(j + 1) * p.nvec]
+            xg = xg_all[j * p.nvec:(j + 1) * p.nvec]
+            u = stats[s * nrhs + j]
+            _, so = orc.gadi(b, a, 1.0, prec, tol=1e-10, maxit=3000, tol_h=tol_in, tol_s=tol_in,
+                             s_pointwise=True)
+            assert so["status"] == "OK" and u["status"] == G.OK
+            assert abs(u["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+            rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
+            assert rel <= 1e-10
+            assert u["seconds"] > 0
+    for h in handles:
+        h.close()
+
+
+def test_batched_rejects_other_classes():
+    import torch
+    from workloads import conv_diff_3d
+    p, _ = conv_diff_3d(4, 5)
+    with G.Gadi.from_problem(p) as H:
+        b = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        st, _ = G.solve_batched([H], 1, [b], [x], [1.0], check=False)
+    assert st == G.ERR_UNSUPPORTED

@@ -162,3 +162,37 @@ def test_norm2_estimate():
         est = H.norm2(200)
     true = np.linalg.norm(A, 2)
     assert 0.999 * true <= est <= true * (1 + 1e-10)
+
+
+def test_alpha_restarts_recover_from_stagnation():
+    """Sec. 4.3 step 3: a BF16 run with a too-small alpha stagnates; with
+    restarts, alpha is doubled from the last iterate until it converges."""
+    p, xt = conv_diff_2d(48, 9)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    a = alpha_star(p) / 16
+    import torch
+    with G.Gadi.from_problem(p) as H:
+        x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+        st, s = H.solve(dev64(b), x, a, 1.0, BF16, 1e-10, 5000, outer_stag_window=5)
+        assert st == G.STAGNATED
+        x.zero_()
+        st, s = H.solve(dev64(b), x, a, 1.0, BF16, 1e-10, 5000, outer_stag_window=5, alpha_restarts=10)
+    assert st == G.OK, G.status_str(st)
+    assert s["restarts"] >= 1 and s["alpha"] > a
+    xg = x.cpu().numpy()
+    rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
+    assert rel <= 1e-10 and abs(rel - s["relres"]) <= 1e-2 * rel
+
+
+def test_barrier_wait_runs_out_and_device_stays_usable():
+    """A grid barrier that one block never reaches: the others' bounded waits
+    run out, the kernel unwinds and the host reads GADI_ERR_TIMEOUT; a solve
+    afterwards still works."""
+    assert G.selftest_barrier(64, 50.0) == G.ERR_TIMEOUT
+    p, xt = conv_diff_2d(24, 210)
+    b = O.Oracle(p).rhs(xt)
+    with G.Gadi.from_problem(p) as H:
+        x = np.zeros(p.nvec)
+        st, s = H.solve(b, x, 2 * alpha_star(p), 1.0, FP32, 1e-10, 2000)
+    assert st == G.OK
