@@ -29,11 +29,40 @@ if ROOT not in sys.path:
 
 WORKLOAD = "conv-diff-2d 2048x2048 (n=4194304), beta~U[1,100]^2 seed 2, HSS, tol 1e-10"
 # GADI parameters shared by the mixed and the plain FP64 runs
-ALPHA_FACTOR = 4.0     # alpha = ALPHA_FACTOR * alpha* (closed-form HSS value)
+ALPHA_FACTOR = 8.0     # alpha = ALPHA_FACTOR * alpha* (closed-form HSS value)
 OMEGA = 0.0
 TOL = 1e-10
 MAXIT = 20000
-TOL_INNER = 1e-3
+TOL_INNER = 1e-3       # default inner tolerance (other configurations)
+# 2048^2 inner tolerances, shared by the mixed and the FP64 runs: 1e-2 on the
+# H-solve was faster for FP32 but let plain FP64 GADI stagnate, so both use 1e-3
+TOL_H, TOL_S = 1e-3, 1e-3
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+KERNEL_SOURCES = ["gadi_kernel.cuh", "gadi_solver.cuh", "gadi_common.cuh", "gadi_params.h",
+                  "gadi_inst_2d5.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2512_21164_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(alg_bytes: float):
+    """DRAM bytes of one launch from the committed ncu record (DRAM bytes per
+    algorithmic byte of a capped solve of the same kernel, scaled to this
+    launch), or None if the kernel sources changed since the capture."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+        if rec.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes
+    except Exception:
+        return None
 HBM_FALLBACK = 6800.0
 
 
@@ -136,7 +165,7 @@ def run_ours(args):
     H.apply(G.OP_A, xtd, b)
     x = torch.zeros_like(b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    kw = dict(tol_h=TOL_INNER, tol_s=TOL_INNER)
+    kw = dict(tol_h=TOL_H, tol_s=TOL_S)
 
     def one(prec):
         x.zero_()
@@ -220,7 +249,7 @@ def run_ours(args):
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 outer / f32 inner", "data": "synthetic",
         "config": {"workload": WORKLOAD, "alpha": alpha, "alpha_over_alpha_star": ALPHA_FACTOR,
-                   "omega": OMEGA, "tol_inner": TOL_INNER, "u_s": "fp32", "u": "fp64",
+                   "omega": OMEGA, "tol_h": TOL_H, "tol_s": TOL_S, "u_s": "fp32", "u": "fp64",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed (256 MB write) before each step"},
         "status": G.status_str(mixed_status), "outer_its": mixed_stats["outer_its"],
@@ -229,7 +258,7 @@ def run_ours(args):
         "fp64_plain": fp64,
         "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                     "frac": achieved / hbm, "traffic": measured_traffic(ab), "peak_source": src,
                      "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve)",
                      "algorithmic_bytes": ab},
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n,
@@ -249,8 +278,9 @@ def run_ours(args):
 
 def run_profile_case(args):
     """A small, bounded launch for ncu: one solve of the benchmark workload
-    capped at --maxit outer iterations (the first kernel launch is the FP64
-    operator application that forms b; the solve is the second)."""
+    (or, with --workload c3, of the 3D workload at --grid3) capped at --maxit
+    outer iterations (the first kernel launch is the FP64 operator
+    application that forms b; the solve is the second)."""
     import torch
 
     import paper_2512_21164_gb300 as G
@@ -258,14 +288,18 @@ def run_profile_case(args):
     from workloads import alpha_star, config2
     B.build()
     prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[args.profile_case]
-    p, xt = config2(args.grid)
+    if args.workload == "c3":
+        from workloads import config3
+        p, xt = config3(args.grid3)
+    else:
+        p, xt = config2(args.grid)
     H = G.Gadi.from_problem(p)
     xtd = torch.from_numpy(xt).cuda()
     b = torch.zeros_like(xtd)
     H.apply(G.OP_A, xtd, b)
     x = torch.zeros_like(b)
-    st, s = H.solve(b, x, ALPHA_FACTOR * alpha_star(p), OMEGA, prec, TOL, args.maxit,
-                    tol_h=TOL_INNER, tol_s=TOL_INNER)
+    af = args.alpha_factor if args.workload == "c3" else ALPHA_FACTOR
+    st, s = H.solve(b, x, af * alpha_star(p), OMEGA, prec, TOL, args.maxit, tol_h=TOL_H, tol_s=TOL_S)
     print(json.dumps({"profile_case": args.profile_case, "status": G.status_str(st), **s}))
 
 
@@ -335,6 +369,55 @@ def run_workload(args):
                          "peak_source": src}}), flush=True)
 
 
+def run_batched(args):
+    """Config 5: 96 uneven 2D systems x 4 right-hand sides in one persistent
+    launch (FP32 inner, FP64 outer), literal alpha ~ logU[1e-2,10] capped at
+    --maxit5 outer iterations per unit, and a batch with alpha = alpha*(N) x
+    logU[0.5,2].  Reports solves/s (converged units per second of the launch),
+    the converged fraction and p50/p99 of the per-unit device times."""
+    import numpy as np
+    import torch
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import config5
+    B.build()
+    for scaled in (False, True):
+        systems = config5(args.nsys5, 4, scaled_alpha=scaled)
+        hs, bs, xs, al = [], [], [], []
+        for p, a, xts in systems:
+            H = G.Gadi.from_problem(p)
+            xt = torch.from_numpy(np.concatenate(xts)).cuda()
+            b = torch.zeros_like(xt)
+            for j in range(4):
+                H.apply(G.OP_A, xt[j * p.nvec:(j + 1) * p.nvec], b[j * p.nvec:(j + 1) * p.nvec])
+            hs.append(H)
+            bs.append(b)
+            xs.append(torch.zeros_like(b))
+            al.append(a)
+        maxit = args.maxit5 if not scaled else 20000
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        st, stats = G.solve_batched(hs, 4, bs, xs, al, OMEGA, G.FP32, TOL, maxit, tol_h=TOL_INNER,
+                                    tol_s=TOL_INNER, batch_group=args.group5)
+        ev1.record()
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        conv = [u for u in stats if u["status"] == G.OK]
+        t = np.array([u["seconds"] for u in conv]) if conv else np.array([0.0])
+        print(json.dumps({
+            "metric": "batched GADI solves/s (time to 1e-10 per unit)", "workload": "c5",
+            "config": {"workload": f"{len(systems)} 2D conv-diff systems N in {{128,256,512,1024}}, 4 rhs each",
+                       "alpha": "alpha*(N) x logU[0.5,2]" if scaled else "logU[1e-2,10]", "omega": OMEGA,
+                       "maxit": maxit, "u_s": "fp32", "batch_group": args.group5},
+            "value": len(conv) / sec, "unit": "solves/s", "seconds": sec, "units": len(stats),
+            "converged": len(conv), "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
+            "status": G.status_str(st)}), flush=True)
+        for H in hs:
+            H.close()
+
+
 def cpu_baseline(p, xt, alpha, gpu_stats, outer):
     """The CPU oracle timed on a bounded sample: `outer` outer iterations of
     Algorithm 1 (FP64 outer, FP32 inner) on the full grid, scaled to the
@@ -343,7 +426,7 @@ def cpu_baseline(p, xt, alpha, gpu_stats, outer):
     orc = O.Oracle(p)
     b = orc.rhs(xt)
     t0 = time.perf_counter()
-    _, st = orc.gadi(b, alpha, OMEGA, O.FP32, tol=0.0, maxit=outer, tol_h=TOL_INNER, tol_s=TOL_INNER,
+    _, st = orc.gadi(b, alpha, OMEGA, O.FP32, tol=0.0, maxit=outer, tol_h=TOL_H, tol_s=TOL_S,
                      outer_stag_window=0)
     dt = time.perf_counter() - t0
     per_outer = dt / max(1, st["outer_its"])
@@ -400,15 +483,20 @@ def main():
     ap.add_argument("--ref-outer", type=int, default=2800)
     ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
                     help="run one solve capped at --maxit outer iterations (for ncu) and exit")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
                     help="c2 (default): the headline line; others: per-precision lines")
     ap.add_argument("--grid3", type=int, default=512)
     ap.add_argument("--grid4", type=int, default=4096)
-    ap.add_argument("--alpha-factor", type=float, default=ALPHA_FACTOR)
+    ap.add_argument("--alpha-factor", type=float, default=4.0)
     ap.add_argument("--fp64-maxit", type=int, default=20000)
+    ap.add_argument("--maxit5", type=int, default=2000)
+    ap.add_argument("--nsys5", type=int, default=96)
+    ap.add_argument("--group5", type=int, default=8)
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+    elif args.workload == "c5" and args.impl == "ours":
+        run_batched(args)
     elif args.workload != "c2" and args.impl == "ours":
         run_workload(args)
     elif args.impl == "reference":

@@ -265,17 +265,31 @@ __device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (
     const int lane = threadIdx.x & 31;
     const int nstrips = (ne + 32 * W - 1) / (32 * W);
     const int collen = D3 ? nz : ny;
-    const int ncols = D3 ? nstrips * ny : nstrips;
     const long long mstride = D3 ? (long long)ne * ny : (long long)ne;
+    // 2D: warps split (strip, row) units.  3D: blocks split (strip, y-tile, z)
+    // units; the warps of a block take consecutive y rows of one tile and
+    // march the same z range, so each warp's y-neighbour rows are the rows
+    // its neighbour warps load at the same time (L1 hits).
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    const int nyt = D3 ? (ny + nwb - 1) / nwb : 1;
+    const int ncols = D3 ? nstrips * nyt : nstrips;
     int u, u1;
-    split_units(ncols * collen, vg, u, u1);
+    if constexpr (D3) {
+        const int nb = vg.n, bi = vg.b, nu = ncols * collen;
+        const int q = nu / nb, rem = nu - q * nb;
+        u = bi * q + min(bi, rem);
+        u1 = u + q + (bi < rem ? 1 : 0);
+    } else {
+        split_units(ncols * collen, vg, u, u1);
+    }
     while (u < u1) {
         const int col = u / collen;
         const int m0 = u - col * collen;
         const int m1 = min(collen, m0 + (u1 - u));
         u += m1 - m0;
-        const int strip = D3 ? col / ny : col;
-        const int yy = D3 ? col - strip * ny : 0;
+        const int strip = D3 ? col / nyt : col;
+        const int yy = D3 ? (col - strip * nyt) * nwb + wib : 0;
+        if (D3 && yy >= ny) continue; // past the last row of a partial tile
         const int e0 = strip * 32 * W + lane * W;
         const bool act = e0 < ne;
         const long long cbase = (D3 ? (long long)yy * ne : 0ll) + e0;

@@ -207,15 +207,22 @@ def config4(n: int = 4096):
     return complex_rd(n, SEED_C4)
 
 
-def config5(nsys: int = 96, nrhs: int = 4, sizes=(128, 256, 512, 1024), seed: int = SEED_C5):
+def config5(nsys: int = 96, nrhs: int = 4, sizes=(128, 256, 512, 1024), seed: int = SEED_C5,
+            scaled_alpha: bool = False):
     """Batched: per-system grid N from `sizes`, beta ~ U[1,100]^2,
-    alpha ~ logU[1e-2, 10]; nrhs right-hand sides each from x_true ~ U[0,1)."""
+    alpha ~ logU[1e-2, 10] (or, with scaled_alpha, alpha* of the grid times
+    logU[0.5, 2]); nrhs right-hand sides each from x_true ~ U[0,1)."""
     g = SplitMix64(seed)
     systems = []
     for s in range(nsys):
         n = sizes[min(int(g.uniform() * len(sizes)), len(sizes) - 1)]
         beta = (1.0 + 99.0 * g.uniform(), 1.0 + 99.0 * g.uniform())
-        alpha = math.exp(math.log(1e-2) + (math.log(10.0) - math.log(1e-2)) * g.uniform())
+        if scaled_alpha:
+            t = math.pi / (2 * (n + 1))
+            a_star = math.sqrt((8 * math.sin(t) ** 2) * (8 * math.cos(t) ** 2))
+            alpha = a_star * math.exp(math.log(0.5) + (math.log(2.0) - math.log(0.5)) * g.uniform())
+        else:
+            alpha = math.exp(math.log(1e-2) + (math.log(10.0) - math.log(1e-2)) * g.uniform())
         p = Problem(K_2D5, n, n, 1, 1.0 / (n + 1), (beta[0], beta[1], 0.0), name=f"sys{s} {n}^2")
         xts = [g.uniform_array(n * n) for _ in range(nrhs)]
         systems.append((p, alpha, xts))
