@@ -104,7 +104,7 @@ typedef struct {
 /* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2
  * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
- * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0. */
+ * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 1. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
     double tol_s;          /* inner CGNR tolerance on S (normal residual)   */
@@ -122,6 +122,13 @@ typedef struct {
     int alpha_restarts;    /* Sec. 4.3 step 3: on STAGNATED or DIVERGED,
                               double alpha and continue from the last finite
                               iterate, up to this many times (0 = off)      */
+    int h_resident;        /* 2D real class, FP32/BF16, 16-byte aligned rows:
+                              1 = CG on H keeps its search direction p in
+                              shared memory when a block's rows (+2 halo
+                              rows) fit without lowering occupancy; 0 =
+                              always stream p through global memory.  Same
+                              arithmetic either way; only the order of the
+                              grid-wide sums differs.                       */
 } gadi_opts;
 
 typedef struct {
@@ -135,6 +142,7 @@ typedef struct {
     int blocks;             /* persistent blocks launched                    */
     double alpha;           /* alpha of the last run (after any restarts)    */
     int restarts;           /* alpha restarts taken (Sec. 4.3 step 3)        */
+    int h_resident;         /* 1 if the H-solve kept p in shared memory      */
 } gadi_stats;
 
 typedef struct gadi_handle gadi_handle;
@@ -214,6 +222,16 @@ gadi_status gadi_select_alpha(const gadi_problem *prob, double alpha0, gadi_prec
  * Errors: INVALID (nblocks < 2 or above the co-resident maximum, timeout_ms
  * not in (0, 10000]), CUDA. */
 gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms);
+
+/* Check of the library's integer-pipe number conversions (no counterpart in
+ * the paper): for each of the n doubles at `in` (DEVICE pointer, n >= 0),
+ * compares on the device (1) binary64 -> binary32 round-to-nearest-even,
+ * (2) binary64 -> BF16 round-to-nearest-even, both against the hardware
+ * conversion, and (3) binary32 -> binary64 of the float whose bits are the
+ * low 32 bits of the input, against the hardware widening -- all bit for
+ * bit.  mismatches (HOST array of 3) receives the count per check.  Synchronous
+ * on the legacy default stream.  Errors: INVALID (n < 0, null pointers), CUDA. */
+gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches);
 
 /* y = Op x in FP64 for Op in {A, M, N, A^T} (Sec. 3.1 splitting).  x and y
  * may be host or device memory; stream as in gadi_opts (NULL = default). */

@@ -46,14 +46,15 @@ class Opts(C.Structure):
     _fields_ = [("tol_h", C.c_double), ("tol_s", C.c_double), ("maxit_inner", C.c_int),
                 ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
                 ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
-                ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int)]
+                ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int),
+                ("h_resident", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("outer_its", C.c_int), ("inner_its_h", C.c_longlong),
                 ("inner_its_s", C.c_longlong), ("relres", C.c_double), ("r0_norm", C.c_double),
                 ("seconds", C.c_double), ("status", C.c_int), ("blocks", C.c_int),
-                ("alpha", C.c_double), ("restarts", C.c_int)]
+                ("alpha", C.c_double), ("restarts", C.c_int), ("h_resident", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +102,8 @@ def lib():
             L.gadi_select_alpha.restype = C.c_int
             L.gadi_selftest_barrier.argtypes = [C.c_int, C.c_double]
             L.gadi_selftest_barrier.restype = C.c_int
+            L.gadi_selftest_convert.argtypes = [vp, C.c_longlong, C.POINTER(C.c_longlong)]
+            L.gadi_selftest_convert.restype = C.c_int
             L.gadi_solve_h_2d_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, vp, vp,
                                                   C.c_double, C.c_int, C.c_int, ip, vp]
             for f in ("gadi_create", "gadi_solve", "gadi_apply", "gadi_norm2_estimate",
@@ -267,6 +270,17 @@ def selftest_barrier(nblocks=64, timeout_ms=50.0):
     """gadi_selftest_barrier: a grid barrier whose wait runs out; returns the status
     (GADI_ERR_TIMEOUT expected)."""
     return lib().gadi_selftest_barrier(int(nblocks), float(timeout_ms))
+
+
+def selftest_convert(d):
+    """gadi_selftest_convert on a device float64 tensor: mismatch counts of the
+    integer-pipe conversions (f64->f32, f64->bf16, f32->f64) against the
+    hardware ones."""
+    out = (C.c_longlong * 3)()
+    st = lib().gadi_selftest_convert(_ptr(d), int(d.numel()), out)
+    if st != OK:
+        raise GadiError(st, "gadi_selftest_convert")
+    return list(out)
 
 
 def _problem_struct(p):

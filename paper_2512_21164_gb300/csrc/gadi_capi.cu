@@ -279,13 +279,15 @@ bool params_aligned(const Params &P)
     return true;
 }
 
-const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem)
+const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem, int *vec_out = nullptr)
 {
     *smem = 0;
+    if (vec_out) *vec_out = 0;
     if (h->kind == GADI_CSR) return kernel_csr(prec);
     const long long ne = (long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1);
     const int vec = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
     const int v = aligned && (ne % vec) == 0;
+    if (vec_out) *vec_out = v;
     if (h->kind == GADI_STENCIL_2D5) {
         *smem = kernel_2d5_smem(prec, v);
         return kernel_2d5(prec, v);
@@ -311,7 +313,8 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     const bool al = params_aligned(P);
     if (!al && h->kind == GADI_COMPLEX_2D5) return GADI_ERR_INVALID; // complex vectors: 16-byte aligned
     size_t smem = 0;
-    const void *k = pick_kernel(h, prec, al, &smem);
+    int vec = 0;
+    const void *k = pick_kernel(h, prec, al, &smem, &vec);
     if (!k) return GADI_ERR_UNSUPPORTED;
     if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -319,6 +322,30 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     if (per_sm <= 0) return GADI_ERR_CUDA;
     int blocks = per_sm * h->nsm;
     if (max_blocks > 0) blocks = std::min(blocks, max_blocks);
+    // SM-resident H-solve: block b keeps rows [b ny / G, (b+1) ny / G) of p
+    // plus one halo row on each side in shared memory (floats); taken only
+    // where every block owns at least one row and the extra shared memory
+    // keeps the blocks this launch needs co-resident on each SM
+    if (P.resident) {
+        P.resident = 0;
+        if (h->kind == GADI_STENCIL_2D5 && prec != P_FP64 && vec && blocks <= h->ny &&
+            (P.mode == MODE_SOLVE || P.mode == MODE_SOLVE_H)) {
+            const long long rows = (h->ny + blocks - 1) / blocks;
+            const size_t rs = (size_t)(rows + 2) * (size_t)h->nx * sizeof(float);
+            int optin = 0;
+            CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+            const size_t rsz = std::max(rs, smem);
+            if (rsz <= (size_t)optin) {
+                CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
+                int per_sm_r = 0;
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k, kThreadsHost, rsz));
+                if ((long long)per_sm_r * h->nsm >= blocks) {
+                    P.resident = 1;
+                    smem = rsz;
+                }
+            }
+        }
+    }
     gadi_status s = ensure_ctl(h, blocks, std::max(P.maxit, 1));
     if (s != GADI_OK) return s;
     P.part = h->d_part;
@@ -410,6 +437,18 @@ __global__ void k_nonfinite(const double *v, long long n, int *flag)
 }
 
 // block 0 never arrives: the other blocks' barrier waits run out
+// integer-pipe conversions against the hardware ones (gadi_selftest_convert)
+__global__ void k_selftest_convert(const double *in, long long n, unsigned long long *bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = in[i];
+        if (__float_as_uint(f64_to_f32_fast(d)) != __float_as_uint(__double2float_rn(d))) atomicAdd(bad, 1ull);
+        if (f64_to_bf16_fast(d) != f64_to_bf16(d)) atomicAdd(bad + 1, 1ull);
+        const float g = __uint_as_float((uint32_t)__double_as_longlong(d));
+        if (__double_as_longlong(f32_to_f64_fast(g)) != __double_as_longlong((double)g)) atomicAdd(bad + 2, 1ull);
+    }
+}
+
 __global__ void k_barrier_selftest(unsigned long long *counter, int *abort_flag, unsigned long long timeout_ns)
 {
     if (blockIdx.x == 0) return;
@@ -503,6 +542,7 @@ gadi_status opts_check(const gadi_opts &o)
 {
     if (!(o.tol_h >= 0) || !(o.tol_s >= 0) || o.maxit_inner < 0 || o.inner_stag < 0 || o.outer_stag_window < 0)
         return GADI_ERR_INVALID;
+    if (o.h_resident != 0 && o.h_resident != 1) return GADI_ERR_INVALID;
     return GADI_OK;
 }
 
@@ -527,6 +567,7 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->hist = nullptr;
     o->batch_group = 0;
     o->alpha_restarts = 0;
+    o->h_resident = 1;
 }
 
 const char *gadi_last_error(void) { return g_last_error; }
@@ -743,6 +784,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
     P.inner_stag = o.inner_stag;
     P.outer_win = o.outer_stag_window;
     P.pointwise = o.s_pointwise;
+    P.resident = o.h_resident;
     CK(cudaEventRecord(h->ev0, st));
     int blocks = 0;
     if ((s = launch(h, prec, P, o.max_blocks, st, &blocks)) != GADI_OK) return s;
@@ -767,6 +809,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
         stats->blocks = blocks;
         stats->alpha = alpha;
         stats->restarts = 0;
+        stats->h_resident = P.resident;
     }
     return (gadi_status)c.status;
 }
@@ -801,6 +844,24 @@ double unit_roundoff(int prec) { return prec == P_BF16 ? 3.91e-3 : (prec == P_FP
 } // namespace
 
 extern "C" {
+
+gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches)
+{
+    if (!in || !mismatches || n < 0) return GADI_ERR_INVALID;
+    unsigned long long *d_bad = nullptr, hb[3] = {0, 0, 0};
+    CK(cudaMalloc(&d_bad, sizeof hb));
+    cudaError_t e = cudaMemset(d_bad, 0, sizeof hb);
+    if (e == cudaSuccess && n > 0) {
+        const long long nb = std::min<long long>((n + 255) / 256, 4096);
+        k_selftest_convert<<<(unsigned)nb, 256>>>(in, n, d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) return cuda_err(e, "gadi_selftest_convert", __LINE__);
+    for (int k = 0; k < 3; k++) mismatches[k] = (long long)hb[k];
+    return GADI_OK;
+}
 
 gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms)
 {
@@ -1038,6 +1099,9 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.seconds = (double)(ht[nunits + q] - ht[q]) * 1e-9;
             S.status = c.status;
             S.blocks = gsize;
+            S.alpha = alpha[u / nrhs];
+            S.restarts = 0;
+            S.h_resident = 0;
         }
     }
     return worst;
@@ -1147,6 +1211,7 @@ gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, con
     P.maxit_inner = maxit;
     P.inner_stag = stag;
     P.maxit = 1;
+    P.resident = 1;
     if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;
     if ((s = finish(h, st)) != GADI_OK) return s;
     if (its) *its = (int)h->h_ctl->inner_h;

@@ -43,6 +43,63 @@ __device__ __forceinline__ uint16_t f64_to_bf16(double d)
 }
 
 // ---------------------------------------------------------------------------
+// binary32/BF16 <-> binary64 conversions on the integer pipe.  On GB300 the
+// hardware conversions between FP32 and FP64 issue on the FP64 pipe, at about
+// 2 per clock per SM (the same rate as an FP64 fused multiply-add, against
+// some 64 integer operations), and the FP64 residual of each outer iteration
+// is bound by that pipe.  The common cases -- zero and results in the normal
+// binary32 range -- are therefore assembled from the IEEE 754 fields
+// (sign, biased exponent, significand) with integer operations; subnormal,
+// infinite, NaN and out-of-range cases fall back to the hardware conversion.
+// The results equal the hardware conversions bit for bit (checked on the
+// device by gadi_selftest_convert).
+// ---------------------------------------------------------------------------
+// exact widening: rebias the exponent (1023 - 127 = 896), shift the
+// 23-bit significand into the top of the 52-bit one
+__device__ __forceinline__ double f32_to_f64_fast(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)u, 0);
+    return (double)f;
+}
+// round to nearest, ties to even, keeping `keep` of the 52 significand bits:
+// the top `keep` bits with the exponent above them, plus one if the discarded
+// part exceeds half an ulp or equals it with an odd kept part (a carry out of
+// the significand moves into the exponent, and past the largest finite
+// exponent gives infinity, as rounding requires)
+template <int KEEP>
+__device__ __forceinline__ uint32_t f64_round_fields(uint64_t u, uint32_t e32)
+{
+    constexpr int DROP = 52 - KEEP;
+    const uint64_t mant = u & 0xfffffffffffffull;
+    uint32_t bits = (e32 << KEEP) | (uint32_t)(mant >> DROP);
+    const uint64_t rem = mant & ((1ull << DROP) - 1ull), half = 1ull << (DROP - 1);
+    bits += (rem > half || (rem == half && (bits & 1u))) ? 1u : 0u;
+    return bits;
+}
+__device__ __forceinline__ float f64_to_f32_fast(double d)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(d);
+    const uint32_t ed = (uint32_t)(u >> 52) & 0x7ffu, sign = (uint32_t)(u >> 32) & 0x80000000u;
+    if (ed - 897u < 254u) return __uint_as_float(sign | f64_round_fields<23>(u, ed - 896u));
+    if ((u << 1) == 0ull) return __uint_as_float(sign);
+    return __double2float_rn(d);
+}
+__device__ __forceinline__ uint16_t f64_to_bf16_fast(double d)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(d);
+    const uint32_t ed = (uint32_t)(u >> 52) & 0x7ffu, sign = (uint32_t)(u >> 48) & 0x8000u;
+    if (ed - 897u < 254u) return (uint16_t)(sign | f64_round_fields<7>(u, ed - 896u));
+    if ((u << 1) == 0ull) return (uint16_t)sign;
+    return f64_to_bf16(d);
+}
+
+// ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type C, elements per 16 bytes
 // ---------------------------------------------------------------------------
 template <int P> struct Prec;
@@ -57,15 +114,15 @@ template <> struct Prec<P_FP32> {
     using S = float; using C = float; static constexpr int VEC = 4;
     __device__ static C ld(S s) { return s; }
     __device__ static S st(C c) { return c; }
-    __device__ static S from_f64(double d) { return __double2float_rn(d); }
-    __device__ static double to_f64(S s) { return (double)s; }
+    __device__ static S from_f64(double d) { return f64_to_f32_fast(d); }
+    __device__ static double to_f64(S s) { return f32_to_f64_fast(s); }
 };
 template <> struct Prec<P_BF16> {
     using S = uint16_t; using C = float; static constexpr int VEC = 8;
     __device__ static C ld(S s) { return bf16_to_f32(s); }
     __device__ static S st(C c) { return f32_to_bf16(c); }
-    __device__ static S from_f64(double d) { return f64_to_bf16(d); }
-    __device__ static double to_f64(S s) { return (double)bf16_to_f32(s); }
+    __device__ static S from_f64(double d) { return f64_to_bf16_fast(d); }
+    __device__ static double to_f64(S s) { return f32_to_f64_fast(bf16_to_f32(s)); }
 };
 
 // ---------------------------------------------------------------------------

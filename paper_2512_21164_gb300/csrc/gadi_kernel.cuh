@@ -21,6 +21,11 @@
 namespace gadi {
 
 constexpr int kThreads = 256;
+// the SM-resident H-solve phases are compiled as separate functions so that
+// their register needs do not reshape the code of the streaming phases
+#ifndef GADI_RES_FN
+#define GADI_RES_FN __noinline__
+#endif
 // resident blocks per SM the register budget is sized for (256 threads each)
 #ifndef GADI_MIN_BLOCKS
 #define GADI_MIN_BLOCKS 2
@@ -546,14 +551,25 @@ struct PhResidual {
         }
         double r[W];
         S so[W];
+        // ||r_s||^2 is summed in FP32 double-word arithmetic (about 48
+        // significand bits) instead of FP64 -- the square of a u_s value is
+        // formed exactly by a product and its fma error term -- so that the
+        // FP64 pipe carries only the residual itself.  acc[1] holds the pair
+        // (hi, lo) of floats in its two 32-bit halves during the sweep.
+        float hi = __int_as_float(__double2hiint(acc[1])), lo = __int_as_float(__double2loint(acc[1]));
 #pragma unroll
         for (int v = 0; v < W; v++) {
             r[v] = __dsub_rn(o.v[0][v], ax[v]);
             acc[0] = fma(r[v], r[v], acc[0]);
             so[v] = PT::from_f64(r[v]);
-            const double sv = PT::to_f64(so[v]);
-            acc[1] = fma(sv, sv, acc[1]);
+            const float sf = PT::ld(so[v]);
+            const float p = __fmul_rn(sf, sf), pe = __fmaf_rn(sf, sf, -p);
+            const float t = __fadd_rn(hi, p), bp = __fsub_rn(t, hi);
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp)); // Knuth's TwoSum
+            hi = t;
+            lo = __fadd_rn(lo, __fadd_rn(err, pe));
         }
+        acc[1] = __hiloint2double(__float_as_int(hi), __float_as_int(lo));
         VecIO<double, W>::store(xo + g, c);
         VecIO<S, W>::store(rs + g, so);
         if (rout) VecIO<double, W>::store(rout + g, r);
@@ -828,10 +844,10 @@ struct StencilImpl {
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
         PhResidual<PREC, WR, K, D3> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca};
-        double a[2] = {0.0, 0.0};
+        double a[2] = {0.0, 0.0}; // a[1]: the float pair (hi, lo), both +0
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
-        acc[1] = a[1];
+        acc[1] = (double)__int_as_float(__double2hiint(a[1])) + (double)__int_as_float(__double2loint(a[1]));
     }
     __device__ void apply(const double *x, double *yout) const
     {
@@ -900,6 +916,182 @@ struct StencilImpl {
         ph.a = a_; ph.first = first; ph.st = ct;
         sweep(ph, acc);
     }
+    // ---- SM-resident H-solve (2D real class, FP32/BF16, 16-byte chunks) ----
+    // Block b owns rows [ya, yb) (a balanced split of the ny rows over the
+    // group's blocks) and keeps p of those rows plus one halo row on each side
+    // in shared memory, as floats holding u_s-rounded values, for the whole
+    // CG solve.  r and z stay in global memory (L2) and are streamed with no
+    // dependency chain.  The halo rows of p are recomputed by this block from
+    // the neighbour's rows of r with the same rounded operations as their
+    // owner: p_0 = r_0 and p_j = fl_s(r_j + beta p_{j-1}), where p_{j-1} of a
+    // halo row is what this block put in the halo slot one iteration before.
+    // By induction the halo equals the owner's rows bit for bit, so blocks
+    // exchange nothing but r, and an iteration keeps its two grid barriers.
+    static constexpr bool RES_OK = (KIND == K_2D5) && (PREC != P_FP64) && (WI * sizeof(S) == 16);
+    __device__ void res_rows(int &ya, int &yb) const
+    {
+        ya = vg.b * ny / vg.n;
+        yb = (vg.b + 1) * ny / vg.n;
+    }
+    __device__ static float *res_smem()
+    {
+        extern __shared__ __align__(16) unsigned char gadi_dsmem[];
+        return reinterpret_cast<float *>(gadi_dsmem);
+    }
+    // chunks of W elements a thread loads before it uses any of them: the
+    // global loads of the resident phases have no dependency chain, so U of
+    // them are kept in flight per thread instead of one per row
+    static constexpr int RES_U = PREC == P_BF16 ? 3 : 4;
+    // p = fl_s(r + beta p_old) on the slab and its halo rows, then the sum of
+    // p.(H p) over the slab
+    __device__ GADI_RES_FN void h1_res(int j, C beta, AT (&acc)[2]) const
+    {
+        if constexpr (RES_OK) {
+            constexpr int W = WI, U = RES_U;
+            using A2 = typename InnerAr<PREC>::T;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            // rows ya-1 .. yb that exist in the grid (the halo slot of a grid
+            // edge stays zero: it is cleared once, at j = 0)
+            const int rlo = ya > 0 ? -1 : 0, rhi = yb < ny ? R : R - 1;
+            const int i_lo = (rlo + 1) * nxw, i_hi = (rhi + 2) * nxw;
+            float *sp = res_smem();
+            const S *r = (const S *)P.r;
+            const bool first = j == 0;
+            if (first) {
+                if (ya == 0)
+                    for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[i] = 0.f;
+                if (yb == ny)
+                    for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[(size_t)(R + 1) * ne + i] = 0.f;
+            }
+            for (int i0 = i_lo + threadIdx.x; i0 < i_hi; i0 += U * blockDim.x) {
+                S rv[U][W];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = i0 + u * blockDim.x;
+                    // element offset of chunk i (>= 0: i >= nxw when ya = 0)
+                    if (i < i_hi) VecIO<S, W>::load(r + ((long long)(ya - 1) * ne + (long long)i * W), rv[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i >= i_hi) break;
+                    float4 *d4 = reinterpret_cast<float4 *>(sp + (size_t)i * W);
+                    float pv[W];
+                    if (first) {
+#pragma unroll
+                        for (int v = 0; v < W; v++) pv[v] = PT::ld(rv[u][v]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < W; v += 4) {
+                            const float4 t = d4[v / 4];
+                            pv[v] = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[u][v]))));
+                            pv[v + 1] = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[u][v + 1]))));
+                            pv[v + 2] = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[u][v + 2]))));
+                            pv[v + 3] = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[u][v + 3]))));
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < W; v += 4) d4[v / 4] = make_float4(pv[v], pv[v + 1], pv[v + 2], pv[v + 3]);
+                }
+            }
+            __syncthreads();
+            AT a = AT(0);
+            const int tin = R * nxw;
+            for (int i = threadIdx.x; i < tin; i += blockDim.x) {
+                const int rr = i / nxw, x0 = (i - rr * nxw) * W;
+                const float *row = sp + (size_t)(rr + 1) * ne;
+                float c[W], w[W], e[W], dn[W], up[W];
+                res_neighbours<W>(row, x0, c, w, e, dn, up);
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    const C q = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], w[v], e[v], dn[v], up[v],
+                                                                C(0), C(0), C(0), false);
+                    a += (AT)c[v] * (AT)q;
+                }
+            }
+            acc[0] = a;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    // z = fl_s(z + a p), r = fl_s(r - a H p) on the slab, p from shared memory
+    __device__ GADI_RES_FN void h2_res(bool first, C a_, AT (&acc)[2]) const
+    {
+        if constexpr (RES_OK) {
+            constexpr int W = WI, U = RES_U;
+            using A2 = typename InnerAr<PREC>::T;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int nxw = ne / W, tot = (yb - ya) * nxw;
+            const float *sp = res_smem();
+            S *z = (S *)P.z, *r = (S *)P.r;
+            const size_t g0 = (size_t)ya * ne;
+            AT s = AT(0);
+            for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
+                S zv[U][W], rv[U][W];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i >= tot) break;
+                    const size_t g = g0 + (size_t)i * W; // slab rows are contiguous
+                    if (!first) VecIO<S, W>::load(z + g, zv[u]);
+                    VecIO<S, W>::load(r + g, rv[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i >= tot) break;
+                    const int rr = i / nxw, x0 = (i - rr * nxw) * W;
+                    const float *row = sp + (size_t)(rr + 1) * ne;
+                    float c[W], w[W], e[W], dn[W], up[W];
+                    res_neighbours<W>(row, x0, c, w, e, dn, up);
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        const C q = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], w[v], e[v], dn[v], up[v],
+                                                                    C(0), C(0), C(0), false);
+                        zv[u][v] = PT::st(first ? A2::mul(a_, c[v]) : A2::madd(a_, c[v], PT::ld(zv[u][v])));
+                        rv[u][v] = PT::st(A2::madd(-a_, q, PT::ld(rv[u][v])));
+                        const C t = PT::ld(rv[u][v]);
+                        s += (AT)t * (AT)t;
+                    }
+                    const size_t g = g0 + (size_t)i * W;
+                    VecIO<S, W>::store(z + g, zv[u]);
+                    VecIO<S, W>::store(r + g, rv[u]);
+                }
+            }
+            acc[0] = s;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    // the slab row `row` (shared memory) at x0..x0+W-1 and its four neighbours
+    template <int W>
+    __device__ void res_neighbours(const float *row, int x0, float (&c)[W], float (&w)[W], float (&e)[W],
+                                   float (&dn)[W], float (&up)[W]) const
+    {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row + x0);
+        const float4 *d4 = reinterpret_cast<const float4 *>(row - ne + x0);
+        const float4 *u4 = reinterpret_cast<const float4 *>(row + ne + x0);
+#pragma unroll
+        for (int v = 0; v < W; v += 4) {
+            const float4 a = r4[v / 4], b = d4[v / 4], t = u4[v / 4];
+            c[v] = a.x; c[v + 1] = a.y; c[v + 2] = a.z; c[v + 3] = a.w;
+            dn[v] = b.x; dn[v + 1] = b.y; dn[v + 2] = b.z; dn[v + 3] = b.w;
+            up[v] = t.x; up[v + 1] = t.y; up[v + 2] = t.z; up[v + 3] = t.w;
+        }
+        const float left = x0 > 0 ? row[x0 - 1] : 0.f;
+        const float right = x0 + W < ne ? row[x0 + W] : 0.f;
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+            w[v] = v > 0 ? c[v - 1] : left;
+            e[v] = v + 1 < W ? c[v + 1] : right;
+        }
+    }
+
     // complex class: S = (alpha + i sigma) I, y = fl_s(g / (alpha + i sigma))
     __device__ void s_pointwise(C gamma) const
     {

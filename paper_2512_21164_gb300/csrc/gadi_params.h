@@ -58,6 +58,7 @@ struct Params {
     // control
     double tol, tol_h, tol_s;
     int maxit, maxit_inner, inner_stag, outer_win, pointwise, first_y_null;
+    int resident;  // 1: the H-solve keeps p in shared memory (2D, FP32/BF16)
     double *part;  // 2 slots x 2 values x gridDim doubles
     double *hist;  // maxit + 1 doubles (device)
     Ctl *ctl;

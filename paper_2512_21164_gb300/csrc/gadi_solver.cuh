@@ -205,6 +205,9 @@ struct CsrImpl {
         return true;
     }
     __device__ void s_pointwise(C) const {}
+    // (the SM-resident H-solve exists for the 2D stencil class only)
+    __device__ void h1r(int, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
+    __device__ void h2r(bool, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
 };
 
 // Adapter giving the stencil implementation the same (bool-returning,
@@ -256,6 +259,8 @@ struct StencilAdapter {
         return true;
     }
     __device__ void s_pointwise(C gamma) const { si.s_pointwise(gamma); }
+    __device__ void h1r(int j, C beta, AT (&acc)[2]) const { si.h1_res(j, beta, acc); }
+    __device__ void h2r(bool first, C a, AT (&acc)[2]) const { si.h2_res(first, a, acc); }
 };
 
 // ---------------------------------------------------------------------------
@@ -317,9 +322,19 @@ struct Runner {
         for (int j = 0; j < P.maxit_inner; ++j) {
             S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
             const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
-            if (!I.h1(j == 0, beta, pold, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            if (P.resident) {
+                I.h1r(j, beta, acc);
+            } else if (!I.h1(j == 0, beta, pold, pnew, acc, gs)) {
+                return -1;
+            }
+            if (!reduce(acc, sum)) return -1;
             const C a = A::div(rr, (C)sum[0]);
-            if (!I.h2(j == 0, a, pnew, acc, gs) || !reduce(acc, sum)) return -1;
+            if (P.resident) {
+                I.h2r(j == 0, a, acc);
+            } else if (!I.h2(j == 0, a, pnew, acc, gs)) {
+                return -1;
+            }
+            if (!reduce(acc, sum)) return -1;
             const C rn = (C)sum[0];
             its = j + 1;
             if (rn <= thr) break;

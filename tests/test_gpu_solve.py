@@ -196,3 +196,37 @@ def test_barrier_wait_runs_out_and_device_stays_usable():
         x = np.zeros(p.nvec)
         st, s = H.solve(b, x, 2 * alpha_star(p), 1.0, FP32, 1e-10, 2000)
     assert st == G.OK
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("max_blocks", [16, 40])
+def test_resident_h_solve_matches_streaming_and_oracle(prec, max_blocks):
+    """The 2D real class with p of CG on H held in shared memory (2-3 rows per
+    block, and exactly one row per block) against the streaming form and the
+    oracle: same arithmetic, only the order of the grid-wide sums differs."""
+    p, xt = conv_diff_2d(48, 201, ny=40)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    alpha = 2 * alpha_star(p)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, alpha, 1.0, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts)
+    res = {}
+    for hr in (1, 0):
+        st, sg, xg, hg = _gpu_solve(p, b, alpha, 1.0, prec, 1e-10, 3000, max_blocks=max_blocks,
+                                    h_resident=hr)
+        assert st == G.OK, G.status_str(st)
+        assert sg["h_resident"] == hr and sg["blocks"] == max_blocks
+        rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
+        assert rel <= 1e-10
+        assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+        res[hr] = sg
+    assert abs(res[1]["outer_its"] - res[0]["outer_its"]) <= max(2, BAND[prec] * res[0]["outer_its"])
+    assert abs(res[1]["inner_its_h"] - res[0]["inner_its_h"]) <= 0.1 * res[0]["inner_its_h"] + 2
+
+
+def test_resident_option_validated():
+    p, xt = conv_diff_2d(16, 206)
+    b = O.Oracle(p).rhs(xt)
+    with G.Gadi.from_problem(p) as H:
+        st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, h_resident=2, check=False)
+    assert st == G.ERR_INVALID

@@ -26,6 +26,10 @@ CASES = {
     "2d_col": lambda: conv_diff_2d(1, 104, ny=70),
     "2d_wide": lambda: conv_diff_2d(1032, 105, ny=9),
     "2d_one": lambda: conv_diff_2d(1, 110, ny=1),
+    # more rows than persistent blocks: the H-solve keeps p in shared memory
+    # (2-3 rows per block, and 1-2 rows per block)
+    "2d_tall": lambda: conv_diff_2d(64, 112, ny=700),
+    "2d_slab1": lambda: conv_diff_2d(40, 113, ny=333),
     "3d_vec": lambda: conv_diff_3d(16, 106),
     "3d_ragged": lambda: (Problem(K_3D7, 7, 5, 9, 1.0 / 8, (13.0, 29.0, 41.0)),
                           SplitMix64(111).uniform_array(7 * 5 * 9)),
@@ -135,7 +139,7 @@ def test_solve_h_fixed_iterations(case, prec):
             assert np.all(np.abs(zg - zo) <= 1.01 * ulp_bf16(zo))
 
 
-@pytest.mark.parametrize("case", ["2d_vec", "2d_wide", "3d_vec", "cplx_vec", "csr"])
+@pytest.mark.parametrize("case", ["2d_vec", "2d_wide", "2d_tall", "3d_vec", "cplx_vec", "csr"])
 @pytest.mark.parametrize("prec", PRECS)
 def test_solve_h_converged(case, prec):
     p, xt = CASES[case]()
@@ -213,3 +217,37 @@ def test_solve_s_converged(case, prec):
 
     rg, ro = true_res(yg), true_res(yo)
     assert rg <= max(3 * ro, 30 * tol), (rg, ro)
+
+
+def test_integer_pipe_conversions_match_hardware():
+    """The binary32/BF16 <-> binary64 conversions the FP64 residual uses are
+    assembled from IEEE 754 fields on the integer pipe; they must equal the
+    hardware conversions bit for bit: random bit patterns over every exponent,
+    round-to-nearest-even ties at the binary32 and BF16 cut, the ends of the
+    binary32 range (smallest normal, largest finite, the tie that rounds to
+    infinity), zeros, subnormals, infinities and NaNs."""
+    import torch
+    g = np.random.default_rng(77)
+    pats = [g.integers(0, 2**63, 200000, dtype=np.uint64) * np.uint64(2) + g.integers(0, 2, 200000, dtype=np.uint64)]
+    # exponents near the binary32 range ends, random significands
+    for e in list(range(890, 905)) + list(range(1140, 1155)):
+        m = g.integers(0, 2**52, 2000, dtype=np.uint64)
+        for sgn in (0, 1):
+            pats.append((np.uint64(sgn) << np.uint64(63)) | (np.uint64(e) << np.uint64(52)) | m)
+    # exact ties and neighbours at the binary32 (bit 29) and BF16 (bit 45) cuts
+    base = g.integers(0, 2**52, 4000, dtype=np.uint64)
+    exps = g.integers(880, 1170, 4000, dtype=np.uint64) << np.uint64(52)
+    for cut in (29, 45):
+        hm = ~np.uint64((1 << cut) - 1) & np.uint64((1 << 52) - 1)
+        tie = (base & hm) | np.uint64(1 << (cut - 1))
+        for t in (tie, tie - np.uint64(1), tie + np.uint64(1)):
+            pats.append(exps | t)
+    specials = np.array([0.0, -0.0, 2.0 ** -126, -(2.0 ** -126), 2.0 ** -127, 2.0 ** -149, 2.0 ** -150,
+                         np.nextafter(2.0 ** -126, 0), (2 - 2.0 ** -23) * 2.0 ** 127,
+                         (2 - 2.0 ** -24) * 2.0 ** 127, np.nextafter((2 - 2.0 ** -24) * 2.0 ** 127, 0),
+                         (2 - 2.0 ** -8) * 2.0 ** 127, np.nextafter((2 - 2.0 ** -8) * 2.0 ** 127, 0),
+                         2.0 ** 128, np.inf, -np.inf, np.nan, 5e-324, 1e-310, 1.0, -1.5, 3.0e38])
+    pats.append(specials.view(np.uint64))
+    allp = np.concatenate(pats).view(np.float64)
+    d = torch.from_numpy(allp.copy()).cuda()
+    assert G.selftest_convert(d) == [0, 0, 0]
