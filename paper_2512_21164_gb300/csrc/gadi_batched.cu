@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
         if (u >= B.nunits) return;
         const Params &P = B.units[u];
         {
-            StencilAdapter<SI> I(P, vg);
-            Runner<PREC, StencilAdapter<SI>> R(P, I);
+            // (units never take the SM-resident H-solve: a group's blocks share SMs)
+            StencilAdapter<SI, false> I(P, vg);
+            Runner<PREC, StencilAdapter<SI, false>> R(P, I);
             R.run();
         }
         if (!gs.sync()) return;

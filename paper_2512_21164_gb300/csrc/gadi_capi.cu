@@ -22,7 +22,7 @@ using namespace gadi;
 
 namespace {
 
-constexpr int kThreadsHost = 256; // must equal gadi::kThreads
+constexpr int kThreadsHost = GADI_THREADS; // = gadi::kThreads
 
 // --------------------------------------------------------------------------
 // host-side rounding of FP64 scalars to the storage precision u_s

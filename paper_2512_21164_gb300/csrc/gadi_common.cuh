@@ -216,24 +216,39 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
     return *reinterpret_cast<const volatile int *>(p);
 }
 
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 struct GridSync {
     unsigned long long *counter; // zeroed before launch
     int *abort_flag;             // zeroed before launch; 1 = a wait timed out
     unsigned nblocks;
     unsigned long long timeout_ns = kBarrierTimeoutNs;
 
-    // returns false if this block must unwind (timeout here or elsewhere)
+    // Arrival is one acquire-release add per block (after a block barrier,
+    // so it publishes the whole block's writes); the block whose add
+    // completes the count goes on at once, the others poll with acquire
+    // loads.  Returns false if this block must unwind (timeout here or
+    // elsewhere).
     __device__ bool sync() const
     {
         __shared__ int s_ok;
         __syncthreads();
         if (threadIdx.x == 0) {
             int ok = 1;
-            __threadfence();
-            unsigned long long arrived = atomicAdd(counter, 1ull) + 1ull;
-            unsigned long long target = ((arrived + nblocks - 1) / nblocks) * nblocks;
-            if (ld_acquire_u64(counter) < target) {
-                unsigned long long t0 = globaltimer_ns();
+            const unsigned long long arrived = atom_add_acq_rel_u64(counter, 1ull) + 1ull;
+            // the count this barrier completes at: arrived rounded up to a
+            // multiple of nblocks (32-bit division while the count fits)
+            const unsigned long long target =
+                (arrived >> 32) == 0ull
+                    ? (unsigned long long)((((unsigned)arrived + nblocks - 1u) / nblocks) * nblocks)
+                    : ((arrived + nblocks - 1ull) / nblocks) * nblocks;
+            if (arrived < target) {
+                const unsigned long long t0 = globaltimer_ns();
                 unsigned spins = 0;
                 while (ld_acquire_u64(counter) < target) {
                     if (ld_volatile_int(abort_flag)) { ok = 0; break; }
@@ -245,7 +260,6 @@ struct GridSync {
                     __nanosleep(32);
                 }
             }
-            __threadfence();
             s_ok = ok;
         }
         __syncthreads();
@@ -291,30 +305,35 @@ __device__ __forceinline__ void block_partials_write(const RT (&v)[NV], RT *part
 template <int NV, class RT>
 __device__ __forceinline__ void grid_partials_sum(const RT *part, int G, RT (&out)[NV])
 {
-    // One warp reads all G partials with independent, unrolled loads (one L2
-    // round trip), sums them in a fixed order and broadcasts through shared
-    // memory.
+    // One warp issues the loads of all NV x G partials before it adds any of
+    // them (one L2 round trip for G <= 32 U), sums them in a fixed order and
+    // broadcasts through shared memory.
     __shared__ RT res[NV];
-    constexpr int U = 8;
+    constexpr int U = 10;
     if ((threadIdx.x >> 5) == 0) {
         const int lane = threadIdx.x & 31;
+        RT s[NV];
 #pragma unroll
-        for (int k = 0; k < NV; k++) {
-            const RT *pk = part + (size_t)k * G;
-            RT s = RT(0);
-            for (int base = lane; base < G; base += 32 * U) {
-                RT t[U];
+        for (int k = 0; k < NV; k++) s[k] = RT(0);
+        for (int base = lane; base < G; base += 32 * U) {
+            RT t[NV][U];
+#pragma unroll
+            for (int k = 0; k < NV; k++)
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int i = base + 32 * u;
-                    t[u] = i < G ? __ldcg(pk + i) : RT(0);
+                    t[k][u] = i < G ? __ldcg(part + (size_t)k * G + i) : RT(0);
                 }
 #pragma unroll
-                for (int u = 0; u < U; u++) s += t[u];
-            }
+            for (int k = 0; k < NV; k++)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) res[k] = s;
+                for (int u = 0; u < U; u++) s[k] += t[k][u];
+        }
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+            if (lane == 0) res[k] = s[k];
         }
     }
     __syncthreads();

@@ -20,15 +20,15 @@
 
 namespace gadi {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = GADI_THREADS;
 // the SM-resident H-solve phases are compiled as separate functions so that
 // their register needs do not reshape the code of the streaming phases
 #ifndef GADI_RES_FN
 #define GADI_RES_FN __noinline__
 #endif
-// resident blocks per SM the register budget is sized for (256 threads each)
+// resident blocks per SM the register budget is sized for (kThreads each)
 #ifndef GADI_MIN_BLOCKS
-#define GADI_MIN_BLOCKS 2
+#define GADI_MIN_BLOCKS (1024 / GADI_THREADS)
 #endif
 // 1: 2D inner phases stage rows through shared memory (march_smem)
 #ifndef GADI_SMEM_SWEEP

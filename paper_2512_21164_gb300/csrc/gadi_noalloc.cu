@@ -23,7 +23,7 @@ namespace {
 
 constexpr long long kNoAllocMaxElems = 262144; // e.g. a 512 x 512 grid
 constexpr int kNoAllocMaxBlocks = 2048;
-constexpr int kThreadsNA = 256; // block size of the persistent kernel
+constexpr int kThreadsNA = GADI_THREADS; // block size of the persistent kernel
 constexpr size_t kSlab = (size_t)kNoAllocMaxElems * 8; // one vector at FP64, the widest u_s
 constexpr size_t kPartBytes = sizeof(double) * 4 * kNoAllocMaxBlocks;
 constexpr size_t kCtlBytes = 256, kHistBytes = 256, kBarBytes = 256, kAbortBytes = 256;

@@ -4,6 +4,14 @@
 
 namespace gadi {
 
+// threads per block of the persistent kernels (host and device agree on it):
+// one block of 512 threads per SM -- the grid barrier and the grid-wide sums
+// then involve one block per SM, which measured faster than two blocks of
+// 256 at the same thread count
+#ifndef GADI_THREADS
+#define GADI_THREADS 512
+#endif
+
 enum : int { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
 enum : int { K_2D5 = 0, K_3D7 = 1, K_C2D5 = 2, K_CSR = 3 };
 

@@ -45,6 +45,7 @@ struct CsrImpl {
     using A = typename InnerAr<PREC>::T;
     using AT = typename AccT<PREC>::T;
     static constexpr int K = 1;
+    static constexpr bool RESIDENT = false;
     const Params &P;
     VGrid vg;
     int n;
@@ -212,13 +213,15 @@ struct CsrImpl {
 
 // Adapter giving the stencil implementation the same (bool-returning,
 // barrier-taking) interface as the CSR one.
-template <class SI>
+template <class SI, bool RES = true>
 struct StencilAdapter {
     using S = typename SI::S;
     using C = typename SI::C;
     using A = typename SI::A;
     using AT = typename SI::AT;
     static constexpr int K = SI::K;
+    // the SM-resident H-solve is compiled in where it exists and RES allows
+    static constexpr bool RESIDENT = SI::RES_OK && RES;
     SI si;
     VGrid vg;
     __device__ StencilAdapter(const Params &p, VGrid g) : si(p, g), vg(g) {}
@@ -322,14 +325,14 @@ struct Runner {
         for (int j = 0; j < P.maxit_inner; ++j) {
             S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
             const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
-            if (P.resident) {
+            if (Impl::RESIDENT && P.resident) {
                 I.h1r(j, beta, acc);
             } else if (!I.h1(j == 0, beta, pold, pnew, acc, gs)) {
                 return -1;
             }
             if (!reduce(acc, sum)) return -1;
             const C a = A::div(rr, (C)sum[0]);
-            if (P.resident) {
+            if (Impl::RESIDENT && P.resident) {
                 I.h2r(j == 0, a, acc);
             } else if (!I.h2(j == 0, a, pnew, acc, gs)) {
                 return -1;

@@ -26,10 +26,10 @@ CASES = {
     "2d_col": lambda: conv_diff_2d(1, 104, ny=70),
     "2d_wide": lambda: conv_diff_2d(1032, 105, ny=9),
     "2d_one": lambda: conv_diff_2d(1, 110, ny=1),
-    # more rows than persistent blocks: the H-solve keeps p in shared memory
-    # (2-3 rows per block, and 1-2 rows per block)
+    # more rows than persistent blocks (one per SM): the H-solve keeps p in
+    # shared memory (4-5 rows per block, and 1-2 rows per block)
     "2d_tall": lambda: conv_diff_2d(64, 112, ny=700),
-    "2d_slab1": lambda: conv_diff_2d(40, 113, ny=333),
+    "2d_slab1": lambda: conv_diff_2d(40, 113, ny=170),
     "3d_vec": lambda: conv_diff_3d(16, 106),
     "3d_ragged": lambda: (Problem(K_3D7, 7, 5, 9, 1.0 / 8, (13.0, 29.0, 41.0)),
                           SplitMix64(111).uniform_array(7 * 5 * 9)),
