@@ -39,7 +39,7 @@ TOL_INNER = 1e-3       # default inner tolerance (other configurations)
 TOL_H, TOL_S = 1e-3, 1e-3
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 KERNEL_SOURCES = ["gadi_kernel.cuh", "gadi_solver.cuh", "gadi_common.cuh", "gadi_params.h",
-                  "gadi_inst_2d5.cu"]
+                  "gadi_inst_2d5.cu", "gadi_inst_2d5r.cu"]
 
 
 def kernel_source_hash() -> str:
@@ -303,6 +303,40 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "status": G.status_str(st), **s}))
 
 
+def record_traffic(rep: str, case_log: str):
+    """Write the traffic record from an ncu report of the --profile-case solve
+    launch (dram__bytes_read.sum + dram__bytes_write.sum, read with `ncu -i`,
+    no GPU needed) and that run's JSON line (its iteration counts give the
+    launch's algorithmic bytes)."""
+    import csv
+    import subprocess
+    with open(case_log) as f:
+        stats = [json.loads(l) for l in f if l.startswith("{")][-1]
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True,
+                         check=True).stdout
+    rows = list(csv.reader(out.splitlines()))
+    head, units, vals = rows[0], rows[1], rows[-1]
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    got = {}
+    for k, u, v in zip(head, units, vals):
+        if k in ("dram__bytes_read.sum", "dram__bytes_write.sum", "Kernel Name", "gpu__time_duration.sum"):
+            got[k] = (v, u)
+    dram = sum(float(got[k][0].replace(",", "")) * scale[got[k][1]]
+               for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
+    from workloads import config2
+    p, _ = config2()
+    sb = {"fp64": 8, "fp32": 4, "bf16": 2}[stats["profile_case"]]
+    alg = algorithmic_bytes(p.npoints, stats, sb)
+    rec = {"kernel": got["Kernel Name"][0], "case": f"--profile-case {stats['profile_case']}",
+           "outer_its": stats["outer_its"], "inner_its_h": stats["inner_its_h"],
+           "inner_its_s": stats["inner_its_s"], "dram_bytes": dram, "algorithmic_bytes": alg,
+           "dram_bytes_per_algorithmic_byte": dram / alg, "kernel_source_hash": kernel_source_hash(),
+           "source": f"ncu -i {os.path.basename(rep)} (dram__bytes_read.sum + dram__bytes_write.sum)"}
+    with open(TRAFFIC_RECORD, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+
+
 # Other configurations: the same measurement, one JSON line per precision.
 # Not the driver's headline line (that is the 2048^2 default above).
 WORKLOADS = {
@@ -492,8 +526,12 @@ def main():
     ap.add_argument("--maxit5", type=int, default=2000)
     ap.add_argument("--nsys5", type=int, default=96)
     ap.add_argument("--group5", type=int, default=8)
+    ap.add_argument("--record-traffic", nargs=2, metavar=("NCU_REPORT", "PROFILE_CASE_LOG"), default=None,
+                    help="write the committed traffic record from an ncu report of --profile-case")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.record_traffic:
+        record_traffic(*args.record_traffic)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.workload == "c5" and args.impl == "ours":
         run_batched(args)

@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
         const Params &P = B.units[u];
         {
             // (units never take the SM-resident H-solve: a group's blocks share SMs)
-            StencilAdapter<SI, false> I(P, vg);
-            Runner<PREC, StencilAdapter<SI, false>> R(P, I);
+            StencilAdapter<SI> I(P, vg);
+            Runner<PREC, StencilAdapter<SI>> R(P, I);
             R.run();
         }
         if (!gs.sync()) return;

@@ -335,13 +335,15 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
             int optin = 0;
             CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
             const size_t rsz = std::max(rs, smem);
-            if (rsz <= (size_t)optin) {
-                CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
+            const void *kr = kernel_2d5_res(prec);
+            if (kr && rsz <= (size_t)optin) {
+                CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
                 int per_sm_r = 0;
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k, kThreadsHost, rsz));
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, kr, kThreadsHost, rsz));
                 if ((long long)per_sm_r * h->nsm >= blocks) {
                     P.resident = 1;
                     smem = rsz;
+                    k = kr;
                 }
             }
         }

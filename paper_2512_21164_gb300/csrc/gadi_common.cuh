@@ -306,10 +306,11 @@ template <int NV, class RT>
 __device__ __forceinline__ void grid_partials_sum(const RT *part, int G, RT (&out)[NV])
 {
     // One warp issues the loads of all NV x G partials before it adds any of
-    // them (one L2 round trip for G <= 32 U), sums them in a fixed order and
-    // broadcasts through shared memory.
+    // them (one L2 round trip for G <= 32 U: one or two blocks per SM of a
+    // 152-SM GPU), sums them in a fixed order and broadcasts through shared
+    // memory.
     __shared__ RT res[NV];
-    constexpr int U = 10;
+    constexpr int U = GADI_THREADS >= 512 ? 5 : 10;
     if ((threadIdx.x >> 5) == 0) {
         const int lane = threadIdx.x & 31;
         RT s[NV];

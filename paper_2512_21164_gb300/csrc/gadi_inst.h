@@ -5,6 +5,8 @@ namespace gadi {
 // vec = 1 selects the 16-byte vector path (requires the row length in
 // elements to be a multiple of the elements per 16 bytes), 0 the narrow path.
 const void *kernel_2d5(int prec, int vec);
+// the 2D kernel with the SM-resident H-solve (FP32/BF16, 16-byte path; else null)
+const void *kernel_2d5_res(int prec);
 const void *kernel_3d7(int prec, int vec);
 const void *kernel_c2d5(int prec, int vec);
 const void *kernel_csr(int prec);

@@ -21,14 +21,13 @@
 namespace gadi {
 
 constexpr int kThreads = GADI_THREADS;
-// the SM-resident H-solve phases are compiled as separate functions so that
-// their register needs do not reshape the code of the streaming phases
+// the SM-resident H-solve phases (instantiated only in their own kernel)
 #ifndef GADI_RES_FN
-#define GADI_RES_FN __noinline__
+#define GADI_RES_FN __forceinline__
 #endif
 // resident blocks per SM the register budget is sized for (kThreads each)
 #ifndef GADI_MIN_BLOCKS
-#define GADI_MIN_BLOCKS (1024 / GADI_THREADS)
+#define GADI_MIN_BLOCKS (GADI_THREADS >= 512 ? 1 : 512 / GADI_THREADS)
 #endif
 // 1: 2D inner phases stage rows through shared memory (march_smem)
 #ifndef GADI_SMEM_SWEEP
@@ -64,7 +63,16 @@ struct ArFusedD {
     __device__ static double madd(double a, double b, double s) { return fma(a, b, s); }
     __device__ static double div(double a, double b) { return __ddiv_rn(a, b); }
 };
-template <int PREC> struct InnerAr { using T = ArExact<float>; };
+// FP32 (also the compute type of the BF16 inner solves) with fused
+// multiply-add: one rounding per product-and-sum, and half the issue slots
+// of a separate product and sum
+struct ArFusedF {
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ static float madd(float a, float b, float s) { return __fmaf_rn(a, b, s); }
+    __device__ static float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <int PREC> struct InnerAr { using T = ArFusedF; };
 template <> struct InnerAr<P_FP64> { using T = ArFusedD; };
 
 // accumulator type of per-thread partial sums in the inner phases
@@ -941,7 +949,7 @@ struct StencilImpl {
     // chunks of W elements a thread loads before it uses any of them: the
     // global loads of the resident phases have no dependency chain, so U of
     // them are kept in flight per thread instead of one per row
-    static constexpr int RES_U = PREC == P_BF16 ? 3 : 4;
+    static constexpr int RES_U = PREC == P_BF16 ? 2 : 4;
     // p = fl_s(r + beta p_old) on the slab and its halo rows, then the sum of
     // p.(H p) over the slab
     __device__ GADI_RES_FN void h1_res(int j, C beta, AT (&acc)[2]) const
@@ -965,52 +973,41 @@ struct StencilImpl {
                 if (yb == ny)
                     for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[(size_t)(R + 1) * ne + i] = 0.f;
             }
-            for (int i0 = i_lo + threadIdx.x; i0 < i_hi; i0 += U * blockDim.x) {
+            // chunk i covers elements [i W, i W + W) counted from row ya - 1
+            // (i >= nxw whenever ya = 0, so every offset used is >= 0)
+            const long long off0 = (long long)(ya - 1) * ne;
+            const int step = U * (int)blockDim.x;
+            for (int i0 = i_lo + threadIdx.x; i0 < i_hi; i0 += step) {
+                const S *rp = r + (off0 + (long long)i0 * W);
+                float *pp = sp + (size_t)i0 * W;
                 S rv[U][W];
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int i = i0 + u * blockDim.x;
-                    // element offset of chunk i (>= 0: i >= nxw when ya = 0)
-                    if (i < i_hi) VecIO<S, W>::load(r + ((long long)(ya - 1) * ne + (long long)i * W), rv[u]);
-                }
+                for (int u = 0; u < U; u++)
+                    if (i0 + u * (int)blockDim.x < i_hi) VecIO<S, W>::load(rp + (size_t)u * blockDim.x * W, rv[u]);
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i >= i_hi) break;
-                    float4 *d4 = reinterpret_cast<float4 *>(sp + (size_t)i * W);
-                    float pv[W];
-                    if (first) {
+                    if (i0 + u * (int)blockDim.x >= i_hi) break;
+                    float4 *d4 = reinterpret_cast<float4 *>(pp + (size_t)u * blockDim.x * W);
 #pragma unroll
-                        for (int v = 0; v < W; v++) pv[v] = PT::ld(rv[u][v]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < W; v += 4) {
-                            const float4 t = d4[v / 4];
-                            pv[v] = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[u][v]))));
-                            pv[v + 1] = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[u][v + 1]))));
-                            pv[v + 2] = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[u][v + 2]))));
-                            pv[v + 3] = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[u][v + 3]))));
+                    for (int v = 0; v < W; v += 4) {
+                        float4 t;
+                        if (first) {
+                            t = make_float4(PT::ld(rv[u][v]), PT::ld(rv[u][v + 1]), PT::ld(rv[u][v + 2]),
+                                            PT::ld(rv[u][v + 3]));
+                        } else {
+                            t = d4[v / 4];
+                            t.x = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[u][v]))));
+                            t.y = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[u][v + 1]))));
+                            t.z = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[u][v + 2]))));
+                            t.w = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[u][v + 3]))));
                         }
+                        d4[v / 4] = t;
                     }
-#pragma unroll
-                    for (int v = 0; v < W; v += 4) d4[v / 4] = make_float4(pv[v], pv[v + 1], pv[v + 2], pv[v + 3]);
                 }
             }
             __syncthreads();
             AT a = AT(0);
-            const int tin = R * nxw;
-            for (int i = threadIdx.x; i < tin; i += blockDim.x) {
-                const int rr = i / nxw, x0 = (i - rr * nxw) * W;
-                const float *row = sp + (size_t)(rr + 1) * ne;
-                float c[W], w[W], e[W], dn[W], up[W];
-                res_neighbours<W>(row, x0, c, w, e, dn, up);
-#pragma unroll
-                for (int v = 0; v < W; v++) {
-                    const C q = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], w[v], e[v], dn[v], up[v],
-                                                                C(0), C(0), C(0), false);
-                    a += (AT)c[v] * (AT)q;
-                }
-            }
+            res_march<false>(false, C(0), a);
             acc[0] = a;
             acc[1] = AT(0);
         } else {
@@ -1021,74 +1018,151 @@ struct StencilImpl {
     __device__ GADI_RES_FN void h2_res(bool first, C a_, AT (&acc)[2]) const
     {
         if constexpr (RES_OK) {
-            constexpr int W = WI, U = RES_U;
-            using A2 = typename InnerAr<PREC>::T;
-            int ya, yb;
-            res_rows(ya, yb);
-            const int nxw = ne / W, tot = (yb - ya) * nxw;
-            const float *sp = res_smem();
-            S *z = (S *)P.z, *r = (S *)P.r;
-            const size_t g0 = (size_t)ya * ne;
             AT s = AT(0);
-            for (int i0 = threadIdx.x; i0 < tot; i0 += U * blockDim.x) {
-                S zv[U][W], rv[U][W];
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i >= tot) break;
-                    const size_t g = g0 + (size_t)i * W; // slab rows are contiguous
-                    if (!first) VecIO<S, W>::load(z + g, zv[u]);
-                    VecIO<S, W>::load(r + g, rv[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i >= tot) break;
-                    const int rr = i / nxw, x0 = (i - rr * nxw) * W;
-                    const float *row = sp + (size_t)(rr + 1) * ne;
-                    float c[W], w[W], e[W], dn[W], up[W];
-                    res_neighbours<W>(row, x0, c, w, e, dn, up);
-#pragma unroll
-                    for (int v = 0; v < W; v++) {
-                        const C q = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], w[v], e[v], dn[v], up[v],
-                                                                    C(0), C(0), C(0), false);
-                        zv[u][v] = PT::st(first ? A2::mul(a_, c[v]) : A2::madd(a_, c[v], PT::ld(zv[u][v])));
-                        rv[u][v] = PT::st(A2::madd(-a_, q, PT::ld(rv[u][v])));
-                        const C t = PT::ld(rv[u][v]);
-                        s += (AT)t * (AT)t;
-                    }
-                    const size_t g = g0 + (size_t)i * W;
-                    VecIO<S, W>::store(z + g, zv[u]);
-                    VecIO<S, W>::store(r + g, rv[u]);
-                }
-            }
+            res_march<true>(first, a_, s);
             acc[0] = s;
             acc[1] = AT(0);
         } else {
             acc[0] = acc[1] = AT(0);
         }
     }
-    // the slab row `row` (shared memory) at x0..x0+W-1 and its four neighbours
-    template <int W>
-    __device__ void res_neighbours(const float *row, int x0, float (&c)[W], float (&w)[W], float (&e)[W],
-                                   float (&dn)[W], float (&up)[W]) const
+    // Thread -> (column chunk, row part) map of the column marches.  With at
+    // least as many W-element chunks per row as threads, thread t takes the
+    // chunks t, t + blockDim, ... down all slab rows; with fewer, the slab
+    // rows are split into blockDim / nxw parts and thread t takes chunk
+    // t % nxw of part t / nxw.  Every thread makes the same number of steps
+    // (rmax per column pass; steps past its rows touch no memory) so that
+    // the warp shuffles always see the whole warp.
+    struct ResMap {
+        int cx0, ncp, r0, r1, rmax;
+        bool act;
+    };
+    __device__ ResMap res_map(int R, int nxw) const
     {
-        const float4 *r4 = reinterpret_cast<const float4 *>(row + x0);
-        const float4 *d4 = reinterpret_cast<const float4 *>(row - ne + x0);
-        const float4 *u4 = reinterpret_cast<const float4 *>(row + ne + x0);
+        ResMap m;
+        const int t = threadIdx.x, nt = blockDim.x;
+        if (nxw >= nt) {
+            m.cx0 = t;
+            m.ncp = (nxw + nt - 1) / nt;
+            m.r0 = 0;
+            m.r1 = m.rmax = R;
+            m.act = true;
+        } else {
+            const int np = nt / nxw, part = t / nxw;
+            m.cx0 = t - part * nxw;
+            m.ncp = 1;
+            m.act = part < np;
+            m.r0 = m.act ? part * R / np : 0;
+            m.r1 = m.act ? (part + 1) * R / np : 0;
+            m.rmax = (R + np - 1) / np;
+        }
+        return m;
+    }
+    // One march of every thread's column chunks down its slab rows.  p comes
+    // from shared memory: the rows below and at the current one stay in
+    // registers, one new row is read per step, and the west / east
+    // neighbours come from the adjacent lanes (shared memory only at a warp
+    // or part edge).  UPD = false: acc += p.(H p).  UPD = true: the H2
+    // update of z and r, whose rows are prefetched PD steps ahead, and
+    // acc += r.r.
+    template <bool UPD>
+    __device__ void res_march(bool first, C a_, AT &acc) const
+    {
+        constexpr int W = WI, PD = PREC == P_BF16 ? 3 : 4;
+        using A2 = typename InnerAr<PREC>::T;
+        int ya, yb;
+        res_rows(ya, yb);
+        const int R = yb - ya, nxw = ne / W;
+        const float *sp = res_smem();
+        const ResMap m = res_map(R, nxw);
+        const int lane = threadIdx.x & 31;
+        for (int cp = 0; cp < m.ncp; ++cp) {
+            const int cx = m.cx0 + cp * (int)blockDim.x;
+            const bool col = m.act && cx < nxw;
+            const int x0 = col ? cx * W : 0;
+            // the adjacent lanes hold chunks cx - 1 and cx + 1 of the same rows
+            const bool lsh = lane > 0 && cx > 0, rsh = lane < 31 && cx + 1 < nxw;
+            const bool xlo = x0 > 0, xhi = x0 + W < ne;
+            // walking pointers: the next shared-memory row to read (the row
+            // below the current one), and z / r at the current row
+            const float *up_p = sp + (size_t)(m.r0 + 2) * ne + x0;
+            S *zp = (S *)P.z + ((size_t)(ya + m.r0) * ne + x0);
+            S *rp = (S *)P.r + ((size_t)(ya + m.r0) * ne + x0);
+            S zq[PD][W], rq[PD][W];
+            if constexpr (UPD) {
+#pragma unroll
+                for (int k = 0; k < PD; k++) {
+                    if (col && m.r0 + k < m.r1) {
+                        if (!first) VecIO<S, W>::load(zp + (size_t)k * ne, zq[k]);
+                        VecIO<S, W>::load(rp + (size_t)k * ne, rq[k]);
+                    }
+                }
+            }
+            float dn[W], c[W], up[W];
+#pragma unroll
+            for (int v = 0; v < W; v++) dn[v] = c[v] = up[v] = 0.f;
+            if (col) {
+                res_row<W>(up_p - 2 * (size_t)ne, dn);
+                res_row<W>(up_p - (size_t)ne, c);
+            }
+            int left = col ? m.r1 - m.r0 : 0; // rows still to do in this column
+            for (int i0 = 0; i0 < m.rmax; i0 += PD) {
+#pragma unroll
+                for (int k = 0; k < PD; k++) {
+                    if (i0 + k >= m.rmax) break; // the same for every thread
+                    const bool ok = left > 0;
+                    if (ok) res_row<W>(up_p, up);
+                    float cl = __shfl_up_sync(0xffffffffu, c[W - 1], 1);
+                    float cr = __shfl_down_sync(0xffffffffu, c[0], 1);
+                    if (ok) {
+                        if (!lsh) cl = xlo ? up_p[-(ptrdiff_t)ne - 1] : 0.f;
+                        if (!rsh) cr = xhi ? up_p[-(ptrdiff_t)ne + W] : 0.f;
+                        S zv[W], rv[W];
+#pragma unroll
+                        for (int v = 0; v < W; v++) {
+                            const float w = v > 0 ? c[v - 1] : cl, e = v + 1 < W ? c[v + 1] : cr;
+                            const C q = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], w, e, dn[v], up[v],
+                                                                        C(0), C(0), C(0), false);
+                            if constexpr (UPD) {
+                                zv[v] = PT::st(first ? A2::mul(a_, c[v]) : A2::madd(a_, c[v], PT::ld(zq[k][v])));
+                                rv[v] = PT::st(A2::madd(-a_, q, PT::ld(rq[k][v])));
+                                const C t = PT::ld(rv[v]);
+                                acc += (AT)t * (AT)t;
+                            } else {
+                                acc += (AT)c[v] * (AT)q;
+                            }
+                        }
+                        if constexpr (UPD) {
+                            VecIO<S, W>::store(zp, zv);
+                            VecIO<S, W>::store(rp, rv);
+                            if (left > PD) { // refill this slot with the row PD steps ahead
+                                if (!first) VecIO<S, W>::load(zp + (size_t)PD * ne, zq[k]);
+                                VecIO<S, W>::load(rp + (size_t)PD * ne, rq[k]);
+                            }
+                        }
+                    }
+                    --left;
+                    up_p += ne;
+                    zp += ne;
+                    rp += ne;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        dn[v] = c[v];
+                        c[v] = up[v];
+                    }
+                }
+            }
+        }
+    }
+    // W floats of a shared-memory row (16-byte aligned)
+    template <int W>
+    __device__ static void res_row(const float *p, float (&o)[W])
+    {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
 #pragma unroll
         for (int v = 0; v < W; v += 4) {
-            const float4 a = r4[v / 4], b = d4[v / 4], t = u4[v / 4];
-            c[v] = a.x; c[v + 1] = a.y; c[v + 2] = a.z; c[v + 3] = a.w;
-            dn[v] = b.x; dn[v + 1] = b.y; dn[v + 2] = b.z; dn[v + 3] = b.w;
-            up[v] = t.x; up[v + 1] = t.y; up[v + 2] = t.z; up[v + 3] = t.w;
-        }
-        const float left = x0 > 0 ? row[x0 - 1] : 0.f;
-        const float right = x0 + W < ne ? row[x0 + W] : 0.f;
-#pragma unroll
-        for (int v = 0; v < W; v++) {
-            w[v] = v > 0 ? c[v - 1] : left;
-            e[v] = v + 1 < W ? c[v + 1] : right;
+            const float4 t = p4[v / 4];
+            o[v] = t.x; o[v + 1] = t.y; o[v + 2] = t.z; o[v + 3] = t.w;
         }
     }
 

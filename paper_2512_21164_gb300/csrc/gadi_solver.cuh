@@ -213,7 +213,7 @@ struct CsrImpl {
 
 // Adapter giving the stencil implementation the same (bool-returning,
 // barrier-taking) interface as the CSR one.
-template <class SI, bool RES = true>
+template <class SI, bool RES = false>
 struct StencilAdapter {
     using S = typename SI::S;
     using C = typename SI::C;
@@ -478,11 +478,15 @@ struct Runner {
     }
 };
 
-template <int KIND, int PREC, int WI, int WR>
+// RES = true: the instantiation with the SM-resident H-solve (2D real class,
+// FP32/BF16, 16-byte path), a kernel of its own so that its register needs
+// leave the streaming kernels' code alone
+template <int KIND, int PREC, int WI, int WR, bool RES = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
-    StencilAdapter<StencilImpl<KIND, PREC, WI, WR>> I(P, whole_grid());
-    Runner<PREC, StencilAdapter<StencilImpl<KIND, PREC, WI, WR>>> R(P, I);
+    using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR>, RES>;
+    Ad I(P, whole_grid());
+    Runner<PREC, Ad> R(P, I);
     R.run();
 }
 

@@ -129,9 +129,11 @@ def test_solve_h_fixed_iterations(case, prec):
     rs = rnd(prec, xt - 0.5)
     for its in (1, 4):
         zg, it_g, zo, it_o = _solve_h_pair(p, prec, 0.3, rs, 0.0, its, 0)
-        # FP64 uses FMA on the GPU: where the oracle's residual becomes exactly
-        # zero (a 1 x 1 grid after one step) the GPU may keep iterating on noise
-        assert it_g == it_o or (prec == FP64 and it_o < its <= it_g), (it_g, it_o)
+        # with tolerance 0 the oracle stops early only on an exactly zero
+        # residual (a 1 x 1 grid after one step); the GPU's fused
+        # multiply-add leaves the rounding error of that step instead, and
+        # it may go on iterating on it up to the cap
+        assert it_g == it_o or (it_o < its and it_o < it_g <= its), (it_g, it_o)
         err = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
         assert err <= FIXED_TOL[prec] * its, (its, err)
         if its == 1 and prec == BF16:
@@ -173,7 +175,8 @@ def test_solve_s_fixed_iterations(case, prec):
     z = rnd(prec, xt - 0.5)
     for its in (1, 4):
         yg, it_g, yo, it_o = _solve_s_pair(p, prec, 0.02, 0.7, z, 0.0, its, 0, False)
-        assert it_g == it_o
+        # (an exactly zero residual stops the oracle early, as for H)
+        assert it_g == it_o or (it_o < its and it_o < it_g <= its), (it_g, it_o)
         if np.linalg.norm(yo) == 0:
             assert np.linalg.norm(yg) == 0
             continue
