@@ -5,7 +5,7 @@
  * The method (Algorithm 1 of the paper, Sec. 2.3): with the splitting
  * A = M + N (Sec. 3.1, "eq:split"), a regularisation alpha > 0 and an
  * extrapolation omega in [0, 2) (Sec. 1, Lemma 1), repeat
- *     r = b - A x                               in u_r  (FP64 here)
+ *     r = b - A x                               in u_r  (FP64 or double-FP64)
  *     solve (alpha I + M) z = r                 in u_s  (FP64, FP32 or BF16)
  *     solve (alpha I + N) y = (2 - omega) alpha z   in u_s
  *     x = x + y                                 in u    (FP64)
@@ -16,7 +16,8 @@
  * is diagonal (the complex class of Sec. 5.4).
  *
  * Precisions (Sec. 3.1 requires u_r <= u <= u_s; Sec. 5.1 variants):
- *   u = u_r = FP64 (u_high must be GADI_FP64);
+ *   u = FP64 (u_high must be GADI_FP64); u_r = FP64 by default, or double-FP64
+ *   (GADI_FP64X2 in gadi_opts.u_r: unit roundoff about u^2, see below);
  *   u_s = u_low: FP64 (GADI-FP64), FP32 (GADI-FP32) or BF16 storage with FP32
  *   arithmetic (GADI-BF16).  Inner vectors are stored in u_s; dot products and
  *   matrix-vector products are carried in FP32 (FP64 when u_s = FP64).
@@ -63,7 +64,14 @@ typedef enum {
     GADI_ERR_UNSUPPORTED = -6 /* valid request this build does not implement   */
 } gadi_status;
 
-typedef enum { GADI_FP64 = 0, GADI_FP32 = 1, GADI_BF16 = 2 } gadi_prec;
+/* GADI_FP64X2 ("double-FP64", u ~ 2^-104 ~ u^2) is a residual precision only
+ * (gadi_opts.u_r): r = b - A x is formed with every product exact (a product
+ * and its fused-multiply-add error term) and the sum compensated (Knuth's
+ * TwoSum, as in the Dot2 algorithm of Ogita, Rump & Oishi, "Accurate sum and
+ * dot product", SIAM J. Sci. Comput. 26(6), 2005), giving r as an unevaluated
+ * pair hi + lo; r_s is hi + lo rounded to u_s (ties broken by lo in the
+ * normal binary32 range; elsewhere hi is rounded), ||r|| is taken from hi. */
+typedef enum { GADI_FP64 = 0, GADI_FP32 = 1, GADI_BF16 = 2, GADI_FP64X2 = 3 } gadi_prec;
 
 /* Splittings of Sec. 2.1.  Only HSS is used by the paper's experiments
  * (Sec. 5.2-5.4); the others are reserved. */
@@ -104,7 +112,8 @@ typedef struct {
 /* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2
  * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
- * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 1. */
+ * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 1,
+ * u_r = GADI_FP64. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
     double tol_s;          /* inner CGNR tolerance on S (normal residual)   */
@@ -129,6 +138,9 @@ typedef struct {
                               always stream p through global memory.  Same
                               arithmetic either way; only the order of the
                               grid-wide sums differs.                       */
+    gadi_prec u_r;         /* residual precision u_r (Sec. 3.1, u_r <= u):
+                              GADI_FP64 or GADI_FP64X2; every problem
+                              class, single and batched solves             */
 } gadi_opts;
 
 typedef struct {
@@ -253,6 +265,14 @@ gadi_status gadi_norm2_estimate(gadi_handle *h, int iters, double *out, void *st
 gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b, const double *x,
                                const void *y, double *x_out, double *r_out, void *rs,
                                double *rnorm, void *stream);
+
+/* The same step with the residual precision u_r chosen (GADI_FP64 or
+ * GADI_FP64X2, Sec. 3.1): r_out (nullable) receives the FP64 part hi of r,
+ * r_lo_out (nullable) the low part lo (zeros for u_r = FP64).  Errors:
+ * INVALID (bad u_r or u_low, null b / x / x_out / rs, x aliasing x_out). */
+gadi_status gadi_step_residual_ur(gadi_handle *h, gadi_prec u_r, gadi_prec u_low, const double *b,
+                                  const double *x, const void *y, double *x_out, double *r_out,
+                                  double *r_lo_out, void *rs, double *rnorm, void *stream);
 
 /* H-solve (Algorithm 1 line 3): CG on (alpha I + M) z = rs in u_s from z = 0,
  * until ||res|| <= tol ||rs|| (tol = 0: exactly maxit steps), or `stag` steps

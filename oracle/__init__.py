@@ -62,7 +62,7 @@ class _Problem(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("tol_h", C.c_double), ("tol_s", C.c_double), ("maxit_inner", C.c_int),
                 ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
-                ("s_pointwise", C.c_int)]
+                ("s_pointwise", C.c_int), ("ur_dd", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -88,6 +88,10 @@ def lib():
             L.orc_apply.argtypes = [pp, C.c_int, dp, dp]
             L.orc_residual.restype = C.c_double
             L.orc_residual.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp, dp]
+            L.orc_residual_dd.restype = C.c_double
+            L.orc_residual_dd.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp, dp, dp]
+            L.orc_round_pair.restype = C.c_double
+            L.orc_round_pair.argtypes = [C.c_int, C.c_double, C.c_double]
             L.orc_solve_h.restype = C.c_int
             L.orc_solve_h.argtypes = [pp, C.c_double, C.c_int, dp, dp, C.c_double, C.c_int,
                                       C.c_int]
@@ -190,6 +194,17 @@ class Oracle:
                                  _dp(yy) if yy is not None else None, _dp(xo), _dp(r), _dp(rs))
         return xo, r, rs, nrm
 
+    def residual_dd(self, prec, b, x, y=None):
+        """(x_out, r_hi, r_lo, r_s, ||r_hi||): the residual in double-FP64 (u_r
+        about u^2), r = r_hi + r_lo, r_s = the pair rounded to u_s."""
+        b, x = _f64(b), _f64(x)
+        yy = _f64(y) if y is not None else None
+        xo, rh, rl, rs = (np.empty(self.m) for _ in range(4))
+        nrm = lib().orc_residual_dd(C.byref(self.P), prec, _dp(b), _dp(x),
+                                    _dp(yy) if yy is not None else None, _dp(xo), _dp(rh), _dp(rl),
+                                    _dp(rs))
+        return xo, rh, rl, rs, nrm
+
     def solve_h(self, alpha, prec, rs, tol, maxit=1000, stag=10):
         rs = _f64(rs)
         z = np.empty(self.m)
@@ -205,11 +220,13 @@ class Oracle:
 
     def gadi(self, b, alpha, omega, prec, tol=1e-10, maxit=500, x0=None, tol_h=1e-3,
              tol_s=1e-3, maxit_inner=1000, inner_stag=10, outer_stag_window=50,
-             s_pointwise=False):
-        """Algorithm 1.  Returns (x, stats dict with relres history)."""
+             s_pointwise=False, residual_dd=False):
+        """Algorithm 1 (residual_dd: u_r = double-FP64).  Returns (x, stats dict
+        with relres history)."""
         b = _f64(b)
         x = np.zeros(self.m) if x0 is None else _f64(x0).copy()
-        o = _Opts(tol_h, tol_s, maxit_inner, inner_stag, outer_stag_window, int(s_pointwise))
+        o = _Opts(tol_h, tol_s, maxit_inner, inner_stag, outer_stag_window, int(s_pointwise),
+                  int(residual_dd))
         st = _Stats()
         hist = np.zeros(maxit + 2)
         lib().orc_gadi(C.byref(self.P), _dp(b), _dp(x), alpha, omega, prec, tol, maxit,
@@ -238,6 +255,11 @@ def round_bf16(v):
 
 def round_prec(prec, v):
     return lib().orc_round(prec, float(v))
+
+
+def round_pair(prec, hi, lo):
+    """hi + lo rounded to u_s (ties of hi decided by lo in the normal binary32 range)."""
+    return lib().orc_round_pair(prec, float(hi), float(lo))
 
 
 def iteration_matrix(A, M, N, alpha, omega):

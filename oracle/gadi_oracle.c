@@ -613,6 +613,115 @@ double orc_residual(const orc_problem *p, int prec, const double *b, const doubl
     return sqrt(s);
 }
 
+/* ------------------------------------------------------------------------ */
+/* residual in double-FP64 (u_r about u^2; Sec. 3.1 allows any u_r <= u)      */
+/* ------------------------------------------------------------------------ */
+/* Error-free transformations in double: a + b = s + e exactly (Knuth's
+ * TwoSum), a * b = p + e exactly (the error by a fused multiply-add), as used
+ * by the Dot2 algorithm of Ogita, Rump & Oishi, "Accurate sum and dot
+ * product", SIAM J. Sci. Comput. 26(6), 2005. */
+static void ef_sum(double a, double b, double *s, double *e)
+{
+    double ss = a + b;
+    double bb = ss - a;
+    *e = (a - (ss - bb)) + (b - bb);
+    *s = ss;
+}
+static void ef_prod(double a, double b, double *p, double *e)
+{
+    double pp = a * b;
+    *e = fma(a, b, -pp);
+    *p = pp;
+}
+/* (hi, lo) -= a x: the product exact, its high part added by TwoSum, the two
+ * error terms accumulated in lo */
+static void dd_sub(double *hi, double *lo, double a, double x)
+{
+    double p, pe, q;
+    ef_prod(-a, x, &p, &pe);
+    ef_sum(*hi, p, hi, &q);
+    *lo = *lo + (q + pe);
+}
+
+/* hi + lo rounded to u_s (|lo| at most half an ulp of hi).  For |hi| in the
+ * normal binary32 range [2^-126, 2^128): to nearest among numbers with `sig`
+ * significant bits (24 for FP32, 8 for BF16), a tie of hi decided by the sign
+ * of lo (ties to even when lo = 0), overflow to infinity.  Elsewhere hi alone
+ * is rounded.  FP64: hi. */
+double orc_round_pair(int prec, double hi, double lo)
+{
+    if (prec == ORC_FP64) return hi;
+    double a = fabs(hi);
+    if (!(a >= ldexp(1.0, -126) && a < ldexp(1.0, 128))) return orc_round(prec, hi);
+    int sig = prec == ORC_FP32 ? 24 : 8;
+    double beyond = hi < 0 ? -lo : lo; /* > 0: the value lies past hi in magnitude */
+    int e;
+    (void)frexp(a, &e);                /* a in [2^(e-1), 2^e) */
+    int q = e - sig;                   /* spacing of the target numbers there */
+    double sc = ldexp(a, -q);          /* exact; in [2^(sig-1), 2^sig) */
+    double fl = floor(sc), fr = sc - fl;
+    double k;
+    if (fr > 0.5) k = fl + 1.0;
+    else if (fr < 0.5) k = fl;
+    else if (beyond > 0) k = fl + 1.0;
+    else if (beyond < 0) k = fl;
+    else k = fmod(fl, 2.0) == 0.0 ? fl : fl + 1.0;
+    double r = ldexp(k, q);
+    if (r >= ldexp(1.0, 128)) r = INFINITY;
+    return hi < 0 ? -r : r;
+}
+
+/* x_out = x + y (FP64); r = b - A x_out in double-FP64: per row b, then each
+ * term of A's row in the operator's order (centre, W, E, S, N, B, T with zero
+ * outside the grid, then the complex coupling; CSR: the stored row order),
+ * renormalised by TwoSum into r_hi + r_lo; rs = the pair rounded to u_s.
+ * Returns ||r_hi||_2. */
+double orc_residual_dd(const orc_problem *p, int prec, const double *b, const double *x,
+                       const double *y, double *x_out, double *r_hi, double *r_lo, double *rs)
+{
+    gadi_ops g;
+    if (build_ops(p, 1.0, prec, &g)) return -1.0;
+    const orc_op *A = &g.A;
+    int m = op_len(A);
+    for (int i = 0; i < m; i++) x_out[i] = y ? x[i] + y[i] : x[i];
+    if (A->kind == ORC_K_CSR) {
+        for (int i = 0; i < A->n; i++) {
+            double hi = b[i], lo = 0.0;
+            for (int k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) dd_sub(&hi, &lo, A->val[k], x_out[A->col[k]]);
+            ef_sum(hi, lo, &r_hi[i], &r_lo[i]);
+        }
+    } else {
+        int nz = A->kind == ORC_K_3D7 ? A->nz : 1;
+        int ndir = A->kind == ORC_K_3D7 ? 6 : 4;
+        int cplx = A->kind == ORC_K_C2D5;
+        int K = cplx ? 2 : 1;
+        for (int iz = 0; iz < nz; iz++)
+            for (int iy = 0; iy < A->ny; iy++)
+                for (int ix = 0; ix < A->nx; ix++) {
+                    long i = ((long)iz * A->ny + iy) * A->nx + ix;
+                    for (int part = 0; part < K; part++) {
+                        long ii = K * i + part;
+                        double hi = b[ii], lo = 0.0;
+                        dd_sub(&hi, &lo, A->d, x_out[ii]);
+                        for (int dir = 0; dir < ndir; dir++) {
+                            long j = nbr(A, ix, iy, iz, dir);
+                            dd_sub(&hi, &lo, A->c[dir], j >= 0 ? x_out[K * j + part] : 0.0);
+                        }
+                        /* (i e) (xr + i xi) = -e xi + i e xr */
+                        if (cplx) dd_sub(&hi, &lo, part ? A->e : -A->e, x_out[K * i + (1 - part)]);
+                        ef_sum(hi, lo, &r_hi[ii], &r_lo[ii]);
+                    }
+                }
+    }
+    double s = 0.0;
+    for (int i = 0; i < m; i++) {
+        s = s + r_hi[i] * r_hi[i];
+        rs[i] = orc_round_pair(prec, r_hi[i], r_lo[i]);
+    }
+    free_ops(&g);
+    return sqrt(s);
+}
+
 /* y = Op x in FP64 for the operator `which` (OP_A, OP_M, OP_N) of a problem. */
 void orc_apply(const orc_problem *p, int which, const double *x, double *y)
 {
@@ -634,6 +743,7 @@ enum { ORC_OK = 0, ORC_NOT_CONVERGED = 1, ORC_STAGNATED = 2, ORC_DIVERGED = 3 };
 typedef struct {
     double tol_h, tol_s;
     int maxit_inner, inner_stag, outer_stag_window, s_pointwise;
+    int ur_dd; /* 1: the residual in double-FP64 (orc_residual_dd) */
 } orc_opts;
 
 typedef struct {
@@ -655,11 +765,13 @@ int orc_gadi(const orc_problem *p, const double *b, double *x, double alpha, dou
     double *xn = (double *)malloc(sizeof(double) * mm), *r = (double *)malloc(sizeof(double) * mm);
     double *rs = (double *)malloc(sizeof(double) * mm), *z = (double *)malloc(sizeof(double) * mm);
     double *y = (double *)malloc(sizeof(double) * mm);
+    double *rl = (double *)malloc(sizeof(double) * mm);
     memset(st, 0, sizeof *st);
     double r0 = -1.0;
     int status = ORC_NOT_CONVERGED, k;
     for (k = 0;; k++) {
-        double rn = orc_residual(p, prec, b, x, k > 0 ? y : NULL, xn, r, rs);
+        double rn = o->ur_dd ? orc_residual_dd(p, prec, b, x, k > 0 ? y : NULL, xn, r, rl, rs)
+                             : orc_residual(p, prec, b, x, k > 0 ? y : NULL, xn, r, rs);
         memcpy(x, xn, sizeof(double) * m);
         if (k == 0) r0 = rn;
         double rel = (r0 > 0.0) ? rn / r0 : 0.0;
@@ -676,7 +788,7 @@ int orc_gadi(const orc_problem *p, const double *b, double *x, double alpha, dou
     }
     st->outer_its = k;
     st->status = status;
-    free(xn); free(r); free(rs); free(z); free(y);
+    free(xn); free(r); free(rs); free(z); free(y); free(rl);
     free_ops(&g);
     return status;
 }

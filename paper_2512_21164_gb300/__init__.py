@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gadi.h")
 OK, NOT_CONVERGED, STAGNATED, DIVERGED = 0, 1, 2, 3
 ERR_INVALID, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 FP64, FP32, BF16 = 0, 1, 2
+FP64X2 = 3  # double-FP64: a residual precision (gadi_opts.u_r) only
 SPLIT_HSS = 0
 STENCIL_2D5, STENCIL_3D7, COMPLEX_2D5, CSR = 0, 1, 2, 3
 OP_A, OP_M, OP_N, OP_AT = 0, 1, 2, 3
@@ -47,7 +48,7 @@ class Opts(C.Structure):
                 ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
                 ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
                 ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int),
-                ("h_resident", C.c_int)]
+                ("h_resident", C.c_int), ("u_r", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -88,6 +89,8 @@ def lib():
             L.gadi_apply.argtypes = [vp, C.c_int, vp, vp, vp]
             L.gadi_norm2_estimate.argtypes = [vp, C.c_int, dp, vp]
             L.gadi_step_residual.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, dp, vp]
+            L.gadi_step_residual_ur.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, dp, vp]
+            L.gadi_step_residual_ur.restype = C.c_int
             L.gadi_step_solve_h.argtypes = [vp, C.c_double, C.c_int, vp, vp, C.c_double, C.c_int,
                                             C.c_int, ip, vp]
             L.gadi_step_solve_s.argtypes = [vp, C.c_double, C.c_double, C.c_int, vp, vp,
@@ -244,6 +247,17 @@ class Gadi:
                                       _ptr(r_out), _ptr(rs), C.byref(nrm), _stream(stream))
         if st != OK:
             raise GadiError(st, "gadi_step_residual")
+        return nrm.value
+
+    def step_residual_ur(self, u_r, u_low, b, x, y, x_out, r_out, r_lo_out, rs, stream=None):
+        """gadi_step_residual_ur: the residual step in precision u_r (FP64 or
+        FP64X2); returns ||r||."""
+        nrm = C.c_double()
+        st = lib().gadi_step_residual_ur(self.h, int(u_r), int(u_low), _ptr(b), _ptr(x), _ptr(y),
+                                         _ptr(x_out), _ptr(r_out), _ptr(r_lo_out), _ptr(rs),
+                                         C.byref(nrm), _stream(stream))
+        if st != OK:
+            raise GadiError(st, "gadi_step_residual_ur")
         return nrm.value
 
     def step_solve_h(self, alpha, u_low, rs, z, tol, maxit, stag=0, stream=None):

@@ -279,25 +279,25 @@ bool params_aligned(const Params &P)
     return true;
 }
 
-const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem, int *vec_out = nullptr)
+const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem, int *vec_out = nullptr, int dd = 0)
 {
     *smem = 0;
     if (vec_out) *vec_out = 0;
-    if (h->kind == GADI_CSR) return kernel_csr(prec);
+    if (h->kind == GADI_CSR) return kernel_csr(prec, dd);
     const long long ne = (long long)h->nx * (h->kind == GADI_COMPLEX_2D5 ? 2 : 1);
     const int vec = prec == P_FP64 ? 2 : (prec == P_FP32 ? 4 : 8);
     const int v = aligned && (ne % vec) == 0;
     if (vec_out) *vec_out = v;
     if (h->kind == GADI_STENCIL_2D5) {
         *smem = kernel_2d5_smem(prec, v);
-        return kernel_2d5(prec, v);
+        return kernel_2d5(prec, v, dd);
     }
     if (h->kind == GADI_STENCIL_3D7) {
         *smem = kernel_3d7_smem(prec, v);
-        return kernel_3d7(prec, v);
+        return kernel_3d7(prec, v, dd);
     }
     *smem = kernel_c2d5_smem(prec, v);
-    return kernel_c2d5(prec, v);
+    return kernel_c2d5(prec, v, dd);
 }
 
 gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStream_t st, int *blocks_out)
@@ -314,7 +314,7 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     if (!al && h->kind == GADI_COMPLEX_2D5) return GADI_ERR_INVALID; // complex vectors: 16-byte aligned
     size_t smem = 0;
     int vec = 0;
-    const void *k = pick_kernel(h, prec, al, &smem, &vec);
+    const void *k = pick_kernel(h, prec, al, &smem, &vec, P.ur_dd);
     if (!k) return GADI_ERR_UNSUPPORTED;
     if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -335,7 +335,7 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
             int optin = 0;
             CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
             const size_t rsz = std::max(rs, smem);
-            const void *kr = kernel_2d5_res(prec);
+            const void *kr = kernel_2d5_res(prec, P.ur_dd);
             if (kr && rsz <= (size_t)optin) {
                 CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
                 int per_sm_r = 0;
@@ -545,6 +545,7 @@ gadi_status opts_check(const gadi_opts &o)
     if (!(o.tol_h >= 0) || !(o.tol_s >= 0) || o.maxit_inner < 0 || o.inner_stag < 0 || o.outer_stag_window < 0)
         return GADI_ERR_INVALID;
     if (o.h_resident != 0 && o.h_resident != 1) return GADI_ERR_INVALID;
+    if (o.u_r != GADI_FP64 && o.u_r != GADI_FP64X2) return GADI_ERR_INVALID;
     return GADI_OK;
 }
 
@@ -570,6 +571,7 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->batch_group = 0;
     o->alpha_restarts = 0;
     o->h_resident = 1;
+    o->u_r = GADI_FP64;
 }
 
 const char *gadi_last_error(void) { return g_last_error; }
@@ -787,6 +789,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
     P.outer_win = o.outer_stag_window;
     P.pointwise = o.s_pointwise;
     P.resident = o.h_resident;
+    P.ur_dd = o.u_r == GADI_FP64X2;
     CK(cudaEventRecord(h->ev0, st));
     int blocks = 0;
     if ((s = launch(h, prec, P, o.max_blocks, st, &blocks)) != GADI_OK) return s;
@@ -994,7 +997,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     gadi_handle *h0 = hs[0];
     cudaStream_t st = (cudaStream_t)o.stream;
     size_t smem = 0;
-    const void *k = kernel_batched_2d5(prec, vec ? 1 : 0, &smem);
+    const void *k = kernel_batched_2d5(prec, vec ? 1 : 0, &smem, o.u_r == GADI_FP64X2);
     if (!k) return GADI_ERR_UNSUPPORTED;
     if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -1029,6 +1032,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
         P.maxit_inner = o.maxit_inner;
         P.inner_stag = o.inner_stag;
         P.outer_win = o.outer_stag_window;
+        P.ur_dd = o.u_r == GADI_FP64X2;
         P.pointwise = o.s_pointwise;
     }
     // device buffers for this call
@@ -1167,8 +1171,16 @@ gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b,
                                const void *y, double *x_out, double *r_out, void *rs, double *rnorm,
                                void *stream)
 {
+    return gadi_step_residual_ur(h, GADI_FP64, u_low, b, x, y, x_out, r_out, nullptr, rs, rnorm, stream);
+}
+
+gadi_status gadi_step_residual_ur(gadi_handle *h, gadi_prec u_r, gadi_prec u_low, const double *b,
+                                  const double *x, const void *y, double *x_out, double *r_out,
+                                  double *r_lo_out, void *rs, double *rnorm, void *stream)
+{
     if (!h || !b || !x || !x_out || !rs || x_out == x) return GADI_ERR_INVALID;
     if (u_low != GADI_FP64 && u_low != GADI_FP32 && u_low != GADI_BF16) return GADI_ERR_INVALID;
+    if (u_r != GADI_FP64 && u_r != GADI_FP64X2) return GADI_ERR_INVALID;
     const int prec = (int)u_low;
     cudaStream_t st = (cudaStream_t)stream;
     Work w;
@@ -1183,6 +1195,10 @@ gadi_status gadi_step_residual(gadi_handle *h, gadi_prec u_low, const double *b,
     P.y = (void *)y;
     P.x1 = x_out;
     P.r_out = r_out;
+    P.r_lo_out = r_lo_out;
+    P.ur_dd = u_r == GADI_FP64X2;
+    // an FP64 residual has no low part
+    if (r_lo_out && !P.ur_dd) CK(cudaMemsetAsync(r_lo_out, 0, sizeof(double) * (size_t)h->nelem, st));
     P.r = rs;
     P.maxit = 1;
     if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;

@@ -72,14 +72,18 @@ __device__ __forceinline__ double f32_to_f64_fast(float f)
 // part exceeds half an ulp or equals it with an odd kept part (a carry out of
 // the significand moves into the exponent, and past the largest finite
 // exponent gives infinity, as rounding requires)
+// `beyond` breaks an exact tie for a value that is the double plus a small
+// remainder of the sign it gives: +1 (the value lies past the cut: round
+// up), -1 (short of it: round down), 0 (no remainder: ties to even).
 template <int KEEP>
-__device__ __forceinline__ uint32_t f64_round_fields(uint64_t u, uint32_t e32)
+__device__ __forceinline__ uint32_t f64_round_fields(uint64_t u, uint32_t e32, int beyond = 0)
 {
     constexpr int DROP = 52 - KEEP;
     const uint64_t mant = u & 0xfffffffffffffull;
     uint32_t bits = (e32 << KEEP) | (uint32_t)(mant >> DROP);
     const uint64_t rem = mant & ((1ull << DROP) - 1ull), half = 1ull << (DROP - 1);
-    bits += (rem > half || (rem == half && (bits & 1u))) ? 1u : 0u;
+    const bool up = rem > half || (rem == half && (beyond > 0 || (beyond == 0 && (bits & 1u))));
+    bits += up ? 1u : 0u;
     return bits;
 }
 __device__ __forceinline__ float f64_to_f32_fast(double d)
@@ -99,6 +103,43 @@ __device__ __forceinline__ uint16_t f64_to_bf16_fast(double d)
     return f64_to_bf16(d);
 }
 
+// the unevaluated pair hi + lo (|lo| <= ulp(hi)/2) rounded to binary32 /
+// BF16: hi's rounding, except that an exact tie of hi is decided by lo's
+// sign; outside the normal binary32 range hi alone is rounded
+__device__ __forceinline__ int f64x2_beyond(double hi, double lo)
+{
+    return lo == 0.0 ? 0 : ((lo > 0.0) == (hi > 0.0) ? 1 : -1);
+}
+__device__ __forceinline__ float f64x2_to_f32(double hi, double lo)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(hi);
+    const uint32_t ed = (uint32_t)(u >> 52) & 0x7ffu, sign = (uint32_t)(u >> 32) & 0x80000000u;
+    if (ed - 897u < 254u) return __uint_as_float(sign | f64_round_fields<23>(u, ed - 896u, f64x2_beyond(hi, lo)));
+    return f64_to_f32_fast(hi);
+}
+__device__ __forceinline__ uint16_t f64x2_to_bf16(double hi, double lo)
+{
+    const uint64_t u = (uint64_t)__double_as_longlong(hi);
+    const uint32_t ed = (uint32_t)(u >> 52) & 0x7ffu, sign = (uint32_t)(u >> 48) & 0x8000u;
+    if (ed - 897u < 254u) return (uint16_t)(sign | f64_round_fields<7>(u, ed - 896u, f64x2_beyond(hi, lo)));
+    return f64_to_bf16_fast(hi);
+}
+
+// error-free transformations in FP64: a + b = s + e exactly (Knuth's
+// TwoSum, no ordering condition), a * b = p + e exactly (fused
+// multiply-add), both as in Ogita, Rump & Oishi 2005
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e)
+{
+    p = __dmul_rn(a, b);
+    e = fma(a, b, -p);
+}
+
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type C, elements per 16 bytes
 // ---------------------------------------------------------------------------
@@ -108,6 +149,7 @@ template <> struct Prec<P_FP64> {
     __device__ static C ld(S s) { return s; }
     __device__ static S st(C c) { return c; }
     __device__ static S from_f64(double d) { return d; }
+    __device__ static S from_f64x2(double hi, double) { return hi; }
     __device__ static double to_f64(S s) { return s; }
 };
 template <> struct Prec<P_FP32> {
@@ -115,6 +157,7 @@ template <> struct Prec<P_FP32> {
     __device__ static C ld(S s) { return s; }
     __device__ static S st(C c) { return c; }
     __device__ static S from_f64(double d) { return f64_to_f32_fast(d); }
+    __device__ static S from_f64x2(double hi, double lo) { return f64x2_to_f32(hi, lo); }
     __device__ static double to_f64(S s) { return f32_to_f64_fast(s); }
 };
 template <> struct Prec<P_BF16> {
@@ -122,6 +165,7 @@ template <> struct Prec<P_BF16> {
     __device__ static C ld(S s) { return bf16_to_f32(s); }
     __device__ static S st(C c) { return f32_to_bf16(c); }
     __device__ static S from_f64(double d) { return f64_to_bf16_fast(d); }
+    __device__ static S from_f64x2(double hi, double lo) { return f64x2_to_bf16(hi, lo); }
     __device__ static double to_f64(S s) { return f32_to_f64_fast(bf16_to_f32(s)); }
 };
 

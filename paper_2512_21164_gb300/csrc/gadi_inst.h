@@ -4,18 +4,24 @@
 namespace gadi {
 // vec = 1 selects the 16-byte vector path (requires the row length in
 // elements to be a multiple of the elements per 16 bytes), 0 the narrow path.
-const void *kernel_2d5(int prec, int vec);
+// dd = 1 selects the instantiation whose residual is in double-FP64.
+const void *kernel_2d5(int prec, int vec, int dd = 0);
 // the 2D kernel with the SM-resident H-solve (FP32/BF16, 16-byte path; else null)
-const void *kernel_2d5_res(int prec);
-const void *kernel_3d7(int prec, int vec);
-const void *kernel_c2d5(int prec, int vec);
-const void *kernel_csr(int prec);
+const void *kernel_2d5_res(int prec, int dd = 0);
+const void *kernel_3d7(int prec, int vec, int dd = 0);
+const void *kernel_c2d5(int prec, int vec, int dd = 0);
+const void *kernel_csr(int prec, int dd = 0);
+const void *kernel_2d5_dd(int prec, int vec);
+const void *kernel_2d5_res_dd(int prec);
+const void *kernel_3d7_dd(int prec, int vec);
+const void *kernel_c2d5_dd(int prec, int vec);
 // dynamic shared memory (bytes) the selected stencil kernel needs at launch
 size_t kernel_2d5_smem(int prec, int vec);
 size_t kernel_3d7_smem(int prec, int vec);
 size_t kernel_c2d5_smem(int prec, int vec);
 // the batched persistent kernel for the 2D 5-point class
-const void *kernel_batched_2d5(int prec, int vec, size_t *smem);
+const void *kernel_batched_2d5(int prec, int vec, size_t *smem, int dd = 0);
+const void *kernel_batched_2d5_dd(int prec, int vec, size_t *smem);
 // record a message for gadi_last_error() on this thread
 void record_error(const char *msg);
 } // namespace gadi

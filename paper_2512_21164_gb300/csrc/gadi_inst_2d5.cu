@@ -3,8 +3,9 @@
 #include "gadi_solver.cuh"
 
 namespace gadi {
-const void *kernel_2d5(int prec, int vec)
+const void *kernel_2d5(int prec, int vec, int dd)
 {
+    if (dd) return kernel_2d5_dd(prec, vec);
     switch (prec) {
     case P_FP64:
         return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 2, 2>

@@ -4,8 +4,9 @@
 #include "gadi_solver.cuh"
 
 namespace gadi {
-const void *kernel_2d5_res(int prec)
+const void *kernel_2d5_res(int prec, int dd)
 {
+    if (dd) return kernel_2d5_res_dd(prec);
     switch (prec) {
     case P_FP32:
         return (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, true>;

@@ -3,8 +3,9 @@
 #include "gadi_solver.cuh"
 
 namespace gadi {
-const void *kernel_3d7(int prec, int vec)
+const void *kernel_3d7(int prec, int vec, int dd)
 {
+    if (dd) return kernel_3d7_dd(prec, vec);
     switch (prec) {
     case P_FP64:
         return vec ? (const void *)gadi_stencil_kernel<K_3D7, P_FP64, 2, 2>

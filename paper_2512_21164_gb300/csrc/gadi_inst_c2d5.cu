@@ -4,8 +4,9 @@
 #include "gadi_solver.cuh"
 
 namespace gadi {
-const void *kernel_c2d5(int prec, int vec)
+const void *kernel_c2d5(int prec, int vec, int dd)
 {
+    if (dd) return kernel_c2d5_dd(prec, vec);
     switch (prec) {
     case P_FP64:
         return (const void *)gadi_stencil_kernel<K_C2D5, P_FP64, 2, 2>;

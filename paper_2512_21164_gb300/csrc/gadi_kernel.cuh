@@ -526,7 +526,20 @@ __device__ __forceinline__ void march_smem(const Ph &ph, int ne, int ny, AT (&ac
 // ---------------------------------------------------------------------------
 // R: x_out = x + y, r = b - A x_out (FP64), r_s = fl_s(r); sums ||r||^2 and
 // ||r_s||^2.  With b == nullptr it is the operator application x_out = A x.
-template <int PREC, int W, int K, bool D3>
+// DD: r in double-FP64 (u_r ~ u^2, Sec. 3.1): starting from b, every term
+// -a_j x_j enters as an exact product p + pe (fused multiply-add) added by
+// TwoSum, the errors summed alongside (the Dot2 scheme of Ogita, Rump &
+// Oishi 2005), in the stencil's order (centre, W, E, S, N[, B, T][, the
+// complex coupling]); r = hi + lo after a final TwoSum.
+__device__ __forceinline__ void dd_sub_term(double &hi, double &lo, double a, double x)
+{
+    double p, pe, q;
+    two_prod(-a, x, p, pe);
+    two_sum(hi, p, hi, q);
+    lo = __dadd_rn(lo, __dadd_rn(q, pe));
+}
+
+template <int PREC, int W, int K, bool D3, bool DD = false>
 struct PhResidual {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -539,6 +552,7 @@ struct PhResidual {
     double *rout;
     S *rs;
     Coef7<double> cf;
+    double *rlo; // DD: low parts of r (nullable)
     __device__ void load_own(long long g, Own &o) const
     {
         if (b) VecIO<double, W>::load(b + g, o.v[0]);
@@ -548,16 +562,36 @@ struct PhResidual {
                         const double (&e)[W], const double (&s)[W], const double (&n)[W],
                         const double (&bb)[W], const double (&t)[W], AT (&acc)[2]) const
     {
-        double ax[W];
+        double r[W], rl[W];
+        if constexpr (DD) {
 #pragma unroll
-        for (int v = 0; v < W; v++)
-            ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c, cf.e, c[v], w[v], e[v], s[v], n[v],
-                                                      bb[v], t[v], c[v ^ (K - 1)], (v & 1) != 0);
-        if (b == nullptr) { // operator application: xo = Op x
-            VecIO<double, W>::store(xo + g, ax);
-            return;
+            for (int v = 0; v < W; v++) {
+                double hi = o.v[0][v], lo = 0.0;
+                dd_sub_term(hi, lo, cf.d, c[v]);
+                dd_sub_term(hi, lo, cf.c[0], w[v]);
+                dd_sub_term(hi, lo, cf.c[1], e[v]);
+                dd_sub_term(hi, lo, cf.c[2], s[v]);
+                dd_sub_term(hi, lo, cf.c[3], n[v]);
+                if constexpr (D3) {
+                    dd_sub_term(hi, lo, cf.c[4], bb[v]);
+                    dd_sub_term(hi, lo, cf.c[5], t[v]);
+                }
+                if constexpr (K == 2) dd_sub_term(hi, lo, (v & 1) ? cf.e : -cf.e, c[v ^ 1]);
+                two_sum(hi, lo, r[v], rl[v]);
+            }
+        } else {
+            double ax[W];
+#pragma unroll
+            for (int v = 0; v < W; v++)
+                ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c, cf.e, c[v], w[v], e[v], s[v], n[v],
+                                                          bb[v], t[v], c[v ^ (K - 1)], (v & 1) != 0);
+            if (b == nullptr) { // operator application: xo = Op x
+                VecIO<double, W>::store(xo + g, ax);
+                return;
+            }
+#pragma unroll
+            for (int v = 0; v < W; v++) r[v] = __dsub_rn(o.v[0][v], ax[v]);
         }
-        double r[W];
         S so[W];
         // ||r_s||^2 is summed in FP32 double-word arithmetic (about 48
         // significand bits) instead of FP64 -- the square of a u_s value is
@@ -567,20 +601,22 @@ struct PhResidual {
         float hi = __int_as_float(__double2hiint(acc[1])), lo = __int_as_float(__double2loint(acc[1]));
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            r[v] = __dsub_rn(o.v[0][v], ax[v]);
             acc[0] = fma(r[v], r[v], acc[0]);
-            so[v] = PT::from_f64(r[v]);
+            if constexpr (DD) so[v] = PT::from_f64x2(r[v], rl[v]);
+            else so[v] = PT::from_f64(r[v]);
             const float sf = PT::ld(so[v]);
             const float p = __fmul_rn(sf, sf), pe = __fmaf_rn(sf, sf, -p);
-            const float t = __fadd_rn(hi, p), bp = __fsub_rn(t, hi);
-            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp)); // Knuth's TwoSum
-            hi = t;
+            const float t2 = __fadd_rn(hi, p), bp = __fsub_rn(t2, hi);
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t2, bp)), __fsub_rn(p, bp)); // Knuth's TwoSum
+            hi = t2;
             lo = __fadd_rn(lo, __fadd_rn(err, pe));
         }
         acc[1] = __hiloint2double(__float_as_int(hi), __float_as_int(lo));
         VecIO<double, W>::store(xo + g, c);
         VecIO<S, W>::store(rs + g, so);
         if (rout) VecIO<double, W>::store(rout + g, r);
+        if constexpr (DD)
+            if (rlo) VecIO<double, W>::store(rlo + g, rl);
     }
 };
 
@@ -797,7 +833,9 @@ struct PhS2 {
 // ---------------------------------------------------------------------------
 // stencil implementation of the phase interface
 // ---------------------------------------------------------------------------
-template <int KIND, int PREC, int WI, int WR>
+// DD: the residual phase in double-FP64 (u_r ~ u^2); a separate
+// instantiation, so the FP64-residual kernels carry none of its code
+template <int KIND, int PREC, int WI, int WR, bool DD = false>
 struct StencilImpl {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -851,8 +889,8 @@ struct StencilImpl {
 
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
-        PhResidual<PREC, WR, K, D3> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca};
         double a[2] = {0.0, 0.0}; // a[1]: the float pair (hi, lo), both +0
+        PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out};
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
         acc[1] = (double)__int_as_float(__double2hiint(a[1])) + (double)__int_as_float(__double2loint(a[1]));

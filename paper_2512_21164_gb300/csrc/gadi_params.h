@@ -59,6 +59,7 @@ struct Params {
     // vectors
     const double *b;
     double *x, *x1, *r_out;
+    double *r_lo_out;  // double-FP64 residual: the low part (nullable)
     void *r, *z, *p0, *p1, *y, *u; // u_s storage
     void *q;                       // compute type (CSR only)
     const double *ax_in;           // MODE_APPLY input
@@ -67,6 +68,7 @@ struct Params {
     double tol, tol_h, tol_s;
     int maxit, maxit_inner, inner_stag, outer_win, pointwise, first_y_null;
     int resident;  // 1: the H-solve keeps p in shared memory (2D, FP32/BF16)
+    int ur_dd;     // 1: the residual in double-FP64 (u_r ~ u^2)
     double *part;  // 2 slots x 2 values x gridDim doubles
     double *hist;  // maxit + 1 doubles (device)
     Ctl *ctl;

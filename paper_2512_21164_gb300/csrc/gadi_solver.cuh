@@ -37,7 +37,7 @@ __device__ void phase_zero(void *v, long long m, VGrid vg)
 // whole input vector, so phases that gather from a vector written in the same
 // phase split at an internal grid barrier.
 // ---------------------------------------------------------------------------
-template <int PREC>
+template <int PREC, bool DD = false>
 struct CsrImpl {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -76,14 +76,26 @@ struct CsrImpl {
         double a0 = 0.0, a1 = 0.0;
         S *rs = (S *)P.r;
         for (long long i = i0(); i < n; i += di()) {
-            const double ax = spmv_row<double, double, ArFusedD>(P.rowptr, P.col, P.aval, xout, (int)i);
-            const double r = __dsub_rn(P.b[i], ax);
+            double r, rl = 0.0;
+            S sv;
+            if constexpr (DD) { // double-FP64: b, then -a_ik x_k in row order (as the stencil phase)
+                double hi = P.b[i], lo = 0.0;
+                for (int k = P.rowptr[i]; k < P.rowptr[i + 1]; k++)
+                    dd_sub_term(hi, lo, P.aval[k], __ldcg(xout + P.col[k]));
+                two_sum(hi, lo, r, rl);
+                sv = PT::from_f64x2(r, rl);
+            } else {
+                const double ax = spmv_row<double, double, ArFusedD>(P.rowptr, P.col, P.aval, xout, (int)i);
+                r = __dsub_rn(P.b[i], ax);
+                sv = PT::from_f64(r);
+            }
             a0 = fma(r, r, a0);
-            const S sv = PT::from_f64(r);
             rs[i] = sv;
             const double d = PT::to_f64(sv);
             a1 = fma(d, d, a1);
             if (P.r_out) P.r_out[i] = r;
+            if constexpr (DD)
+                if (P.r_lo_out) P.r_lo_out[i] = rl;
         }
         acc[0] = a0;
         acc[1] = a1;
@@ -481,20 +493,20 @@ struct Runner {
 // RES = true: the instantiation with the SM-resident H-solve (2D real class,
 // FP32/BF16, 16-byte path), a kernel of its own so that its register needs
 // leave the streaming kernels' code alone
-template <int KIND, int PREC, int WI, int WR, bool RES = false>
+template <int KIND, int PREC, int WI, int WR, bool RES = false, bool DD = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
-    using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR>, RES>;
+    using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR, DD>, RES>;
     Ad I(P, whole_grid());
     Runner<PREC, Ad> R(P, I);
     R.run();
 }
 
-template <int PREC>
+template <int PREC, bool DD = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_csr_kernel(const __grid_constant__ Params P)
 {
-    CsrImpl<PREC> I(P, whole_grid());
-    Runner<PREC, CsrImpl<PREC>> R(P, I);
+    CsrImpl<PREC, DD> I(P, whole_grid());
+    Runner<PREC, CsrImpl<PREC, DD>> R(P, I);
     R.run();
 }
 

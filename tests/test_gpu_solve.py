@@ -38,9 +38,10 @@ def _gpu_solve(p, b, alpha, omega, prec, tol, maxit, **kw):
     x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
     hist = np.zeros(maxit + 2)
     th, ts = _tols(prec)
+    opts = dict(tol_h=th, tol_s=ts)
+    opts.update(kw)
     with G.Gadi.from_problem(p) as H:
-        st, stats = H.solve(dev64(b), x, alpha, omega, prec, tol, maxit, hist=hist, tol_h=th,
-                            tol_s=ts, **kw)
+        st, stats = H.solve(dev64(b), x, alpha, omega, prec, tol, maxit, hist=hist, **opts)
     return st, stats, x.cpu().numpy(), hist[:stats["outer_its"] + 1]
 
 
@@ -230,3 +231,44 @@ def test_resident_option_validated():
     with G.Gadi.from_problem(p) as H:
         st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, h_resident=2, check=False)
     assert st == G.ERR_INVALID
+
+
+@pytest.mark.parametrize("name,prec", [("2d", FP32), ("3d", BF16), ("cplx", FP32), ("csr", FP64)])
+def test_double_fp64_residual_solve_matches_oracle(name, prec):
+    """Algorithm 1 with u_r = double-FP64 on the GPU against the oracle's."""
+    p, xt, alpha, omega = {
+        "2d": lambda: (*conv_diff_2d(48, 211, ny=40), None, 1.0),
+        "3d": lambda: (*conv_diff_3d(12, 212), None, 1.0),
+        "cplx": lambda: (*complex_rd(24, 213), None, 1.0),
+        "csr": lambda: (*random_csr(400, 214), 1.0, 1.0),
+    }[name]()
+    if alpha is None:
+        alpha = (1.0 if p.kind == 2 else 2.0) * alpha_star(p)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, alpha, omega, prec, tol=1e-12, maxit=3000, tol_h=th, tol_s=ts, s_pointwise=True,
+                      residual_dd=True)
+    st, sg, xg, hg = _gpu_solve(p, b, alpha, omega, prec, 1e-12, 3000, u_r=G.FP64X2)
+    assert so["status"] == "OK" and st == G.OK, G.status_str(st)
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+    _, rh, rl, _, _ = orc.residual_dd(FP64, b, xg)
+    assert np.linalg.norm(rh) / np.linalg.norm(b) <= 1e-12
+
+
+def test_double_fp64_residual_limits_forward_error_gpu():
+    """Sec. 3 on the GPU: run to stagnation with FP32 inner solves; with
+    u_r = double-FP64 the forward error reaches about u, with u_r = FP64 it
+    stays several times larger (it grows with kappa(A) u_r)."""
+    from test_oracle_residual_dd import forward_error_case, reference_solution
+    p, xt, alpha = forward_error_case()
+    b = O.Oracle(p).rhs(xt)
+    xref = reference_solution(p, b)
+    fe = {}
+    for ur in (G.FP64, G.FP64X2):
+        st, s, xg, _ = _gpu_solve(p, b, alpha, 0.0, FP32, 0.0, 20000, u_r=ur, tol_h=1e-4, tol_s=1e-4,
+                                  outer_stag_window=200)
+        assert st == G.STAGNATED, G.status_str(st)
+        fe[ur] = np.linalg.norm(xg - xref) / np.linalg.norm(xref)
+    assert fe[G.FP64X2] <= 4 * 2.0 ** -53, fe
+    assert fe[G.FP64] >= 4 * fe[G.FP64X2], fe

@@ -254,3 +254,35 @@ def test_integer_pipe_conversions_match_hardware():
     allp = np.concatenate(pats).view(np.float64)
     d = torch.from_numpy(allp.copy()).cuda()
     assert G.selftest_convert(d) == [0, 0, 0]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", PRECS)
+def test_residual_double_fp64_bit_exact(case, prec):
+    """The residual in double-FP64 (u_r ~ u^2): x_out, both parts of r, r_s and
+    ||r|| against the oracle, element by element, with b close to A x so the
+    residual cancels and its low part matters."""
+    import torch
+    p, xt = CASES[case]()
+    orc = O.Oracle(p)
+    m = p.nvec
+    g = SplitMix64(17)
+    x = g.uniform_array(m) - 0.5
+    y = rnd(prec, (g.uniform_array(m) - 0.5) * 1e-2)
+    b = orc.rhs(x + y) + (g.uniform_array(m) - 0.5) * 1e-10
+    with G.Gadi.from_problem(p) as H:
+        xo = torch.zeros(m, dtype=torch.float64, device="cuda")
+        rh, rl = torch.zeros_like(xo), torch.zeros_like(xo)
+        rs = us_empty(m, prec)
+        nrm = H.step_residual_ur(G.FP64X2, prec, dev64(b), dev64(x), us_to_device(y, prec), xo, rh, rl, rs)
+        # u_r = FP64 through the same entry point: the low part is zero
+        rl2 = torch.ones_like(xo)
+        H.step_residual_ur(G.FP64, prec, dev64(b), dev64(x), us_to_device(y, prec), xo, rh.clone(), rl2,
+                           us_empty(m, prec))
+        assert not torch.any(rl2 != 0)
+    xo_o, rh_o, rl_o, rs_o, n_o = orc.residual_dd(prec, b, x, y)
+    assert np.array_equal(xo.cpu().numpy(), xo_o)
+    assert np.array_equal(rh.cpu().numpy(), rh_o)
+    assert np.array_equal(rl.cpu().numpy(), rl_o)
+    assert np.array_equal(us_to_host(rs, prec), rs_o)
+    assert abs(nrm - n_o) <= 1e-12 * n_o
