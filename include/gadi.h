@@ -80,8 +80,8 @@ typedef enum { GADI_SPLIT_HSS = 0 } gadi_splitting;
 /* Problem classes of Sec. 5, plus a general CSR matrix (Sec. 5.1: the
  * paper's own implementation stores A, H and S as sparse matrices). */
 typedef enum {
-    GADI_STENCIL_2D5 = 0, /* -Lap u + beta.grad u, 5-point, Sec. 5.2          */
-    GADI_STENCIL_3D7 = 1, /* 3D convection-diffusion, 7-point, Sec. 5.3       */
+    GADI_STENCIL_2D5 = 0, /* -Lap u + beta.grad u (+ kappa u), 5-point, 5.2   */
+    GADI_STENCIL_3D7 = 1, /* 3D convection-diffusion (+ kappa u), 7-point, 5.3 */
     GADI_COMPLEX_2D5 = 2, /* (L + kappa I) + i sigma I, Sec. 5.4              */
     GADI_CSR = 3          /* general A with positive definite (A + A^T)/2     */
 } gadi_kind;
@@ -91,10 +91,13 @@ typedef enum { GADI_OP_A = 0, GADI_OP_M = 1, GADI_OP_N = 2, GADI_OP_AT = 3 } gad
 
 /* Problem descriptor (Sec. 5.2-5.4).  Stencil matrices are the centred finite
  * differences scaled by h^2 (entries O(1)):
- *   2D: A = M + N, M: centre 4, neighbours -1; N: E +c_x, W -c_x, N +c_y,
- *       S -c_y with c_i = beta_i h / 2;
- *   3D: centre 6 and a third axis;
+ *   2D: A = M + N, M: centre 4 + kappa, neighbours -1; N: E +c_x, W -c_x,
+ *       N +c_y, S -c_y with c_i = beta_i h / 2 (kappa >= 0: an h^2-scaled
+ *       reaction term, as in the problem of Sec. 5.2; 0 for pure
+ *       convection-diffusion);
+ *   3D: centre 6 + kappa and a third axis;
  *   complex: M = L + kappa I (L the 5-point Laplacian), N = i sigma I.
+ *   kappa < 0 is rejected (GADI_ERR_INVALID).
  * h <= 0 means h = 1/(nx+1).  CSR arrays (host memory, 0-based, int32 indices,
  * FP64 values, n rows) are copied by gadi_create; the caller keeps them. */
 typedef struct {
@@ -211,8 +214,8 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
 
 /* Sec. 4.3, step 2: condition numbers of H = alpha I + M and S = alpha I + N
  * from closed forms, for the stencil classes (host only, no GPU work).
- * M's spectrum is the sum of 1D Dirichlet Laplacian spectra (plus kappa for
- * the complex class), so kappa(H) = (alpha + lmax) / (alpha + lmin) exactly.
+ * M's spectrum is the sum of 1D Dirichlet Laplacian spectra plus kappa, so
+ * kappa(H) = (alpha + lmax) / (alpha + lmin) exactly.
  * N is normal with eigenvalues i (sum_i 2 c_i cos(j pi h_i)) (i sigma for the
  * complex class), so kappa(S) <= sqrt(alpha^2 + ||N||^2) / alpha, the value
  * returned (an upper bound; equal when N is singular).  CSR: UNSUPPORTED (no

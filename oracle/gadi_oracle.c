@@ -105,10 +105,12 @@ typedef struct {
 } orc_op;
 
 /* Coefficients of A, M and N for the stencil problems.
- *   2D (Sec. 5.2 with the convection term beta . grad u): A = M + N with
- *     M: centre 4, every neighbour -1 (the h^2-scaled 5-point Laplacian);
+ *   2D (Sec. 5.2 with the convection term beta . grad u and a reaction
+ *   term kappa u, h^2-scaled): A = M + N with
+ *     M: centre 4 + kappa, every neighbour -1 (the h^2-scaled 5-point
+ *     Laplacian plus the reaction);
  *     N: E +c_x, W -c_x, N +c_y, S -c_y, with c_i = beta_i h / 2.
- *   3D (Sec. 5.3): the same with centre 6 and a third axis.
+ *   3D (Sec. 5.3): the same with centre 6 + kappa and a third axis.
  *   complex (Sec. 5.4, W + iT with W = L + kappa I, T = sigma I):
  *     M = W (centre 4 + kappa, neighbours -1), N = i sigma I.
  * out: [0]=d, [1..6]=W,E,S,N,B,T, [7]=e for the requested part
@@ -119,11 +121,11 @@ void orc_stencil_coeffs(int kind, int part, double h, const double *beta,
     double cx = beta[0] * h / 2.0, cy = beta[1] * h / 2.0, cz = beta[2] * h / 2.0;
     double Md = 0, Mc[6] = {0, 0, 0, 0, 0, 0}, Nc[6] = {0, 0, 0, 0, 0, 0}, Ne = 0;
     if (kind == ORC_K_2D5) {
-        Md = 4.0;
+        Md = 4.0 + kappa;
         Mc[0] = Mc[1] = Mc[2] = Mc[3] = -1.0;
         Nc[0] = -cx; Nc[1] = cx; Nc[2] = -cy; Nc[3] = cy;
     } else if (kind == ORC_K_3D7) {
-        Md = 6.0;
+        Md = 6.0 + kappa;
         for (int k = 0; k < 6; k++) Mc[k] = -1.0;
         Nc[0] = -cx; Nc[1] = cx; Nc[2] = -cy; Nc[3] = cy; Nc[4] = -cz; Nc[5] = cz;
     } else { /* complex 2D */

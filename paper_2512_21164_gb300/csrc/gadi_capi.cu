@@ -131,11 +131,11 @@ void stencil_coefs(gadi_handle *h)
     const double cx = h->beta[0] * h->h / 2.0, cy = h->beta[1] * h->h / 2.0, cz = h->beta[2] * h->h / 2.0;
     Stencil M{}, N{};
     if (h->kind == GADI_STENCIL_2D5) {
-        M.d = 4.0;
+        M.d = 4.0 + h->kappa;
         for (int k = 0; k < 4; k++) M.c[k] = -1.0;
         N.c[0] = -cx; N.c[1] = cx; N.c[2] = -cy; N.c[3] = cy;
     } else if (h->kind == GADI_STENCIL_3D7) {
-        M.d = 6.0;
+        M.d = 6.0 + h->kappa;
         for (int k = 0; k < 6; k++) M.c[k] = -1.0;
         N.c[0] = -cx; N.c[1] = cx; N.c[2] = -cy; N.c[3] = cy; N.c[4] = -cz; N.c[5] = cz;
     } else {
@@ -619,6 +619,7 @@ gadi_status gadi_create(const gadi_problem *p, gadi_splitting split, gadi_handle
         for (int k = 0; k < 3; k++)
             if (!std::isfinite(p->beta[k])) st = GADI_ERR_NONFINITE;
         if (!std::isfinite(p->kappa) || !std::isfinite(p->sigma) || !std::isfinite(p->h)) st = GADI_ERR_NONFINITE;
+        if (st == GADI_OK && p->kappa < 0) st = GADI_ERR_INVALID; // M must stay positive definite
         if (st == GADI_OK) {
             h->nx = p->nx;
             h->ny = p->ny;
@@ -835,11 +836,9 @@ bool stencil_spectra(const gadi_problem *p, double *lmin, double *lmax, double *
         hi += 4.0 * std::cos(t) * std::cos(t);
         if (p->kind != GADI_COMPLEX_2D5) nn += 2.0 * std::fabs(p->beta[d] * h / 2.0) * std::cos(2.0 * t);
     }
-    if (p->kind == GADI_COMPLEX_2D5) {
-        lo += p->kappa;
-        hi += p->kappa;
-        nn = std::fabs(p->sigma);
-    }
+    lo += p->kappa;
+    hi += p->kappa;
+    if (p->kind == GADI_COMPLEX_2D5) nn = std::fabs(p->sigma);
     *lmin = lo;
     *lmax = hi;
     *nnorm = nn;

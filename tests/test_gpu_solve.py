@@ -272,3 +272,20 @@ def test_double_fp64_residual_limits_forward_error_gpu():
         fe[ur] = np.linalg.norm(xg - xref) / np.linalg.norm(xref)
     assert fe[G.FP64X2] <= 4 * 2.0 ** -53, fe
     assert fe[G.FP64] >= 4 * fe[G.FP64X2], fe
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+def test_paper_2d_instance_matches_oracle(prec):
+    """Sec. 5.2's own instance (reaction term on the diagonal, strong
+    convection) at 48 x 48 against the oracle."""
+    from workloads import paper_cdr_2d
+    p, xt = paper_cdr_2d(48)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    a = 4 * alpha_star(p)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, a, 0.0, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts)
+    st, sg, xg, hg = _gpu_solve(p, b, a, 0.0, prec, 1e-10, 3000)
+    assert so["status"] == "OK" and st == G.OK, G.status_str(st)
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+    assert np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b) <= 1e-10

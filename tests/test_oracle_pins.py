@@ -436,3 +436,48 @@ def test_config1_trajectory_is_monotone_and_capped():
     h = st["history"]
     assert 1e-9 < h[-1] < 1e-7
     assert np.all(np.diff(h[50:]) < 0)
+
+
+def _tridiag(n, sub, diag, sup):
+    return np.diag(np.full(n, diag)) + np.diag(np.full(n - 1, sub), -1) + np.diag(np.full(n - 1, sup), 1)
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_paper_2d_instance_equals_printed_kronecker_form(n):
+    """Sec. 5.2's matrix as printed: A = I (x) T + T (x) I, T = Tridiag(-1,2,-1)
+    + 2r Tridiag(0.5,0,-0.5) + 100/(n+1)^2 I (Tridiag(sub, diag, super)), r = 1;
+    the workload's (beta, kappa) parametrisation must give exactly it."""
+    from workloads import paper_cdr_2d
+    p, x1 = paper_cdr_2d(n)
+    h2 = 1.0 / (n + 1) ** 2
+    T = _tridiag(n, -1.0, 2.0, -1.0) + 2.0 * _tridiag(n, 0.5, 0.0, -0.5) + 100.0 * h2 * np.eye(n)
+    K = np.kron(np.eye(n), T) + np.kron(T, np.eye(n))
+    orc = O.Oracle(p)
+    assert np.allclose(orc.dense(O.OP_A), K, rtol=0, atol=1e-14)
+    assert np.array_equal(x1, np.ones(n * n))
+    M = orc.dense(O.OP_M)
+    assert np.allclose(M, (K + K.T) / 2, atol=1e-14)
+    assert np.all(np.linalg.eigvalsh(M) > 0)  # M positive definite (Lemma 1's assumption)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_paper_3d_instance_equals_seven_point_kronecker_form(n):
+    """Sec. 5.3's matrix with T_x = T_y = T_z = Tridiag(-1-r, 2, -1+r), r = 1/(2n+2)
+    (the standard 7-point stencil: our reading of the printed diagonal)."""
+    from workloads import paper_cd_3d
+    p, _ = paper_cd_3d(n)
+    r = 1.0 / (2 * n + 2)
+    T = _tridiag(n, -1.0 - r, 2.0, -1.0 + r)
+    I = np.eye(n)
+    K = np.kron(T, np.kron(I, I)) + np.kron(I, np.kron(T, I)) + np.kron(I, np.kron(I, T))
+    assert np.allclose(O.Oracle(p).dense(O.OP_A), K, rtol=0, atol=1e-14)
+
+
+def test_reaction_term_shifts_the_spectrum():
+    """kappa adds kappa I to M (and A) for the real stencil classes."""
+    p0, _ = conv_diff_2d(5, 41, beta=(3.0, 1.0), ny=4)
+    p1, _ = conv_diff_2d(5, 41, beta=(3.0, 1.0), ny=4)
+    p1.kappa = 0.75
+    d0, d1 = O.Oracle(p0).dense(O.OP_M), O.Oracle(p1).dense(O.OP_M)
+    assert np.allclose(d1 - d0, 0.75 * np.eye(20), rtol=0, atol=1e-15)
+    assert np.array_equal(O.Oracle(p1).dense(O.OP_N), O.Oracle(p0).dense(O.OP_N))

@@ -168,6 +168,31 @@ def random_csr(n: int, seed: int, extra_per_row: int = 3, skew: float = 0.5) -> 
     return p, g.uniform_array(n)
 
 
+def paper_cdr_2d(n: int, r: float = 1.0) -> tuple[Problem, np.ndarray]:
+    """The 2D convection-diffusion-reaction instance of Sec. 5.2 on n x n:
+    A = I (x) T + T (x) I, T = Tridiag(-1, 2, -1) + 2r Tridiag(0.5, 0, -0.5)
+    + 100/(n+1)^2 I, r = 1.  With Tridiag(sub, diag, super), T's sub- and
+    super-diagonals are -1 + r and -1 - r: in this module's parametrisation
+    (W = -1 - c_x, E = -1 + c_x, c = beta h / 2) that is c = -r, i.e.
+    beta = -2r/h on both axes.  The reaction enters T_x and T_y, so the
+    diagonal is 4 + 200 h^2 (kappa = 200 h^2), as the printed Kronecker sum
+    gives.  Sec. 5.2 names no right-hand side; b comes from x = (1, ..., 1)
+    as in Sec. 5.3."""
+    h = 1.0 / (n + 1)
+    p = Problem(K_2D5, n, n, 1, h, (-2.0 * r / h, -2.0 * r / h, 0.0), kappa=200.0 * h * h,
+                name=f"paper 2D CDR {n}x{n} (r={r})")
+    return p, np.ones(n * n)
+
+
+def paper_cd_3d(n: int) -> tuple[Problem, np.ndarray]:
+    """The 3D convection-diffusion instance of Sec. 5.3 on n^3: T = Tridiag(
+    -1 - r, ., -1 + r), r = 1/(2n + 2) = h/2 on every axis, i.e. beta =
+    (1, 1, 1); diagonal 6 (the standard 7-point stencil, see the reading on
+    the printed diagonal); b from x = (1, ..., 1)."""
+    p = Problem(K_3D7, n, n, n, 1.0 / (n + 1), (1.0, 1.0, 1.0), name=f"paper 3D CD {n}^3")
+    return p, np.ones(n * n * n)
+
+
 def alpha_star(p: Problem) -> float:
     """Closed-form HSS parameter sqrt(lambda_min(M) lambda_max(M)) for the
     stencil classes (Bai, Golub & Ng 2003, cited in Sec. 2.1): the eigenvalues
