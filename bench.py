@@ -356,11 +356,14 @@ PAPER_TABLE2 = {960: (4.9, 5.1, 3.6), 2560: (44.3, 31.5, 19.9), 4096: (121.0, 84
                 8192: (768.1, 444.6, 307.2), 10000: (1373.0, 779.2, 529.5)}
 PAPER_TABLE3 = {180: (3.9, 2.4, 2.8), 256: (12.2, 7.3, 8.9), 320: (25.7, 15.3, 18.4), 360: (40.2, 23.9, 26.4),
                 400: (62.7, 36.9, 50.3), 450: (101.1, 60.6, 137.3), 512: (None, None, 390.7)}
+# Table 4 (complex reaction-diffusion, tolerance 1e-6)
+PAPER_TABLE4 = {1024: (6.2, 4.0, 2.4), 2048: (21.8, 13.1, 8.1), 4096: (79.6, 46.5, 27.7),
+                5120: (121.7, 72.4, 40.2), 8192: (309.0, 180.2, 98.7)}
 
 
 def run_paper(args):
     """The paper's own instances (Sec. 5.2 2D CDR at tolerance 1e-10, Sec. 5.3
-    3D CD at 1e-6; b from x = ones), at its grid sizes, every inner precision,
+    3D CD and Sec. 5.4 complex RD at 1e-6; b from x = ones), at its grid sizes, every inner precision,
     alpha = f alpha* and omega for each pair in --alpha-factors (the paper
     picks alpha by GPR; the fastest pair is reported).  One JSON line per
     (grid, precision) with the paper's A100 time beside ours."""
@@ -368,16 +371,19 @@ def run_paper(args):
 
     import paper_2512_21164_gb300 as G
     from paper_2512_21164_gb300 import build as B
-    from workloads import alpha_star, paper_cd_3d, paper_cdr_2d
+    from workloads import alpha_star, paper_cd_3d, paper_cdr_2d, paper_complex_rd
     B.build()
-    twod = args.workload == "paper2d"
-    grids = [int(v) for v in args.grids.split(",")] if args.grids else ([960, 2560, 4096] if twod else [180, 256, 320])
-    spec = args.alpha_factors or ("2:0,4:0,8:0" if twod else "0.1:1,0.3:1,1:0")
+    w = args.workload
+    grids = [int(v) for v in args.grids.split(",")] if args.grids else \
+        {"paper2d": [960, 2560, 4096], "paper3d": [180, 256, 320], "paperc": [1024, 2048, 4096]}[w]
+    spec = args.alpha_factors or {"paper2d": "4:0,8:0,16:0", "paper3d": "0.05:1,0.1:1,0.3:1",
+                                  "paperc": "64:1,256:1,1024:1"}[w]
     factors = [(float(v.split(":")[0]), float(v.split(":")[1]) if ":" in v else 0.0) for v in spec.split(",")]
-    tol = 1e-10 if twod else 1e-6
-    table = PAPER_TABLE2 if twod else PAPER_TABLE3
+    tol = 1e-10 if w == "paper2d" else 1e-6
+    table = {"paper2d": PAPER_TABLE2, "paper3d": PAPER_TABLE3, "paperc": PAPER_TABLE4}[w]
+    section = {"paper2d": "2D CDR (Sec. 5.2)", "paper3d": "3D CD (Sec. 5.3)", "paperc": "complex RD (Sec. 5.4)"}[w]
     for n in grids:
-        p, xt = paper_cdr_2d(n) if twod else paper_cd_3d(n)
+        p, xt = {"paper2d": paper_cdr_2d, "paper3d": paper_cd_3d, "paperc": paper_complex_rd}[w](n)
         H = G.Gadi.from_problem(p)
         xtd = torch.from_numpy(xt).cuda()
         b = torch.zeros_like(xtd)
@@ -385,6 +391,8 @@ def run_paper(args):
         x = torch.zeros_like(b)
         a0 = alpha_star(p)
         for j, pn in enumerate(["fp64", "fp32", "bf16"]):
+            if pn not in args.precs.split(","):
+                continue
             prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[pn]
             tin = 1e-2 if pn == "bf16" else TOL_INNER
             runs = []
@@ -399,7 +407,7 @@ def run_paper(args):
             runs.sort(key=lambda r: (r[0], r[1]))
             _, sec, (f, om), st, s, fe = runs[0]
             print(json.dumps({
-                "metric": f"time to {tol:g} relative residual, the paper's {'2D CDR (Sec. 5.2)' if twod else '3D CD (Sec. 5.3)'} instance",
+                "metric": f"time to {tol:g} relative residual, the paper's {section} instance",
                 "workload": args.workload, "grid": n, "n": p.nvec, "u_s": pn, "value": sec, "unit": "s",
                 "status": G.status_str(st), "alpha_over_alpha_star": f, "alpha": s["alpha"], "omega": om,
                 "outer_its": s["outer_its"], "inner_its_h": s["inner_its_h"], "inner_its_s": s["inner_its_s"],
@@ -579,10 +587,11 @@ def main():
     ap.add_argument("--ref-outer", type=int, default=2800)
     ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
                     help="run one solve capped at --maxit outer iterations (for ncu) and exit")
-    ap.add_argument("--grids", default=None, help="paper2d / paper3d: comma-separated grid sizes")
+    ap.add_argument("--grids", default=None, help="paper2d / paper3d / paperc: comma-separated grid sizes")
+    ap.add_argument("--precs", default="fp64,fp32,bf16", help="paper2d / paper3d / paperc: inner precisions")
     ap.add_argument("--alpha-factors", default=None,
                     help="paper2d / paper3d: alpha/alpha*:omega pairs tried (default 2:0,4:0,8:0 / 0.1:1,0.3:1,1:0)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper2d", "paper3d"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper2d", "paper3d", "paperc"],
                     help="c2 (default): the headline line; others: per-precision lines")
     ap.add_argument("--grid3", type=int, default=512)
     ap.add_argument("--grid4", type=int, default=4096)
@@ -600,7 +609,7 @@ def main():
         run_profile_case(args)
     elif args.workload == "c5" and args.impl == "ours":
         run_batched(args)
-    elif args.workload in ("paper2d", "paper3d") and args.impl == "ours":
+    elif args.workload in ("paper2d", "paper3d", "paperc") and args.impl == "ours":
         run_paper(args)
     elif args.workload != "c2" and args.impl == "ours":
         run_workload(args)

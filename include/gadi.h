@@ -110,6 +110,13 @@ typedef struct {
     const int *rowptr;
     const int *col;
     const double *val;
+    /* complex class only (NULL otherwise, or for T = sigma I): a per-point
+     * imaginary diagonal T = diag(T_i), HOST array of nx*ny finite doubles
+     * in grid order (the random potential V(x) of Sec. 5.4), copied by
+     * gadi_create; sigma is then ignored.  S = alpha I + i T stays diagonal
+     * (pointwise solve); its T_i are rounded to u_s like stored
+     * coefficients. */
+    const double *sigma_pt;
 } gadi_problem;
 
 /* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2

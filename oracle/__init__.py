@@ -56,7 +56,8 @@ class _Problem(C.Structure):
                 ("rowptr", C.POINTER(C.c_int)), ("col", C.POINTER(C.c_int)),
                 ("aval", C.POINTER(C.c_double)),
                 ("mrowptr", C.POINTER(C.c_int)), ("mcol", C.POINTER(C.c_int)),
-                ("mval", C.POINTER(C.c_double)), ("nval", C.POINTER(C.c_double))]
+                ("mval", C.POINTER(C.c_double)), ("nval", C.POINTER(C.c_double)),
+                ("sigma_pt", C.POINTER(C.c_double))]
 
 
 class _Opts(C.Structure):
@@ -163,6 +164,11 @@ class Oracle:
             self.split = (mrp, mcl, mv, nv)
         else:
             P.n = prob.npoints
+            sig = getattr(prob, "sigma_pt", None)
+            if prob.kind == K_C2D5 and sig is not None:
+                sg = _f64(sig)
+                self._keep.append(sg)
+                P.sigma_pt = _dp(sg)
         self.P = P
         self.m = prob.nvec
 

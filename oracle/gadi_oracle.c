@@ -98,6 +98,8 @@ typedef struct {
     int nx, ny, nz;
     /* stencil coefficients: d, W, E, S, N, B, T and the imaginary diagonal e */
     double d, c[6], e;
+    /* complex class with a per-point imaginary diagonal: e_i = ep[i] (null: e) */
+    const double *ep;
     /* CSR (kind ORC_K_CSR): y = d*x + V x, V given in CSR */
     int n;
     const int *rowptr, *col;
@@ -207,8 +209,9 @@ static void apply_d(const orc_op *op, const double *x, double *y)
                         }
                     }
                     /* (i e) (xr + i xi) = -e xi + i e xr */
-                    sr = fma(-op->e, x[2 * i + 1], sr);
-                    si = fma(op->e, x[2 * i], si);
+                    double ei = op->ep ? op->ep[i] : op->e;
+                    sr = fma(-ei, x[2 * i + 1], sr);
+                    si = fma(ei, x[2 * i], si);
                     y[2 * i] = sr;
                     y[2 * i + 1] = si;
                 }
@@ -220,6 +223,7 @@ static void apply_d(const orc_op *op, const double *x, double *y)
 typedef struct {
     float d, c[6], e;
     const float *val; /* CSR values rounded to u_s */
+    const float *ep;  /* per-point imaginary diagonal (null: e) */
 } op_f;
 
 static void apply_f(const orc_op *op, const op_f *cf, const float *x, float *y)
@@ -256,8 +260,9 @@ static void apply_f(const orc_op *op, const op_f *cf, const float *x, float *y)
                             si = si + cf->c[dir] * x[2 * j + 1];
                         }
                     }
-                    sr = sr - cf->e * x[2 * i + 1];
-                    si = si + cf->e * x[2 * i];
+                    float ei = cf->ep ? cf->ep[i] : cf->e;
+                    sr = sr - ei * x[2 * i + 1];
+                    si = si + ei * x[2 * i];
                     y[2 * i] = sr;
                     y[2 * i + 1] = si;
                 }
@@ -314,6 +319,9 @@ typedef struct {
     op_f Hf, Sf, Stf;
     float *Mval_f, *Nval_f, *NvalT_f;
     double *Mval_d, *Nval_d, *NvalT_d;
+    /* per-point T of the complex class in u_s: S (+T), S^T (-T), double and float */
+    double *es_d, *est_d;
+    float *es_f, *est_f;
 } gadi_ops;
 
 static void fill_opf(const orc_op *o, op_f *f, const float *val)
@@ -322,6 +330,7 @@ static void fill_opf(const orc_op *o, op_f *f, const float *val)
     for (int k = 0; k < 6; k++) f->c[k] = (float)o->c[k];
     f->e = (float)o->e;
     f->val = val;
+    f->ep = NULL;
 }
 
 /* problem descriptor passed from Python as flat arguments */
@@ -333,6 +342,7 @@ typedef struct {
     const double *aval;       /* A  */
     const int *mrowptr, *mcol; /* M = (A + A^T)/2 pattern; N shares it */
     const double *mval, *nval;
+    const double *sigma_pt; /* complex class: per-point T (nx*ny values) or null */
 } orc_problem;
 
 static int build_ops(const orc_problem *p, double alpha, int prec, gadi_ops *g)
@@ -363,6 +373,26 @@ static int build_ops(const orc_problem *p, double alpha, int prec, gadi_ops *g)
         fill_opf(&g->H, &g->Hf, NULL);
         fill_opf(&g->S, &g->Sf, NULL);
         fill_opf(&g->St, &g->Stf, NULL);
+        if (p->kind == ORC_K_C2D5 && p->sigma_pt) {
+            /* A carries T exactly; S and S^T carry +-T rounded to u_s */
+            size_t np = (size_t)p->nx * p->ny;
+            g->A.ep = p->sigma_pt;
+            g->es_d = (double *)malloc(sizeof(double) * np);
+            g->est_d = (double *)malloc(sizeof(double) * np);
+            g->es_f = (float *)malloc(sizeof(float) * np);
+            g->est_f = (float *)malloc(sizeof(float) * np);
+            if (!g->es_d || !g->est_d || !g->es_f || !g->est_f) return -1;
+            for (size_t i = 0; i < np; i++) {
+                g->es_d[i] = orc_round(prec, p->sigma_pt[i]);
+                g->est_d[i] = -g->es_d[i];
+                g->es_f[i] = (float)g->es_d[i];
+                g->est_f[i] = -g->es_f[i];
+            }
+            g->S.ep = g->es_d;
+            g->St.ep = g->est_d;
+            g->Sf.ep = g->es_f;
+            g->Stf.ep = g->est_f;
+        }
         return 0;
     }
     /* CSR: the pattern of M (= pattern of A + A^T) must hold every diagonal
@@ -408,6 +438,7 @@ static void free_ops(gadi_ops *g)
 {
     free(g->Mval_d); free(g->Nval_d); free(g->NvalT_d);
     free(g->Mval_f); free(g->Nval_f); free(g->NvalT_f);
+    free(g->es_d); free(g->est_d); free(g->es_f); free(g->est_f);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -554,8 +585,8 @@ int orc_solve_s(const orc_problem *p, double alpha, double omega, int prec, cons
         double *gv = w + 4 * m, *t = w + 5 * m;
         for (int i = 0; i < m; i++) gv[i] = gam * z[i];
         if (pointwise && p->kind == ORC_K_C2D5) {
-            double ar = g.S.d, ai = g.S.e, den = ar * ar + ai * ai;
             for (int i = 0; i < m / 2; i++) {
+                double ar = g.S.d, ai = g.S.ep ? g.S.ep[i] : g.S.e, den = ar * ar + ai * ai;
                 double gr = gv[2 * i], gi = gv[2 * i + 1];
                 y[2 * i] = (gr * ar + gi * ai) / den;
                 y[2 * i + 1] = (gi * ar - gr * ai) / den;
@@ -572,8 +603,8 @@ int orc_solve_s(const orc_problem *p, double alpha, double omega, int prec, cons
         float gamf = (float)gam;
         for (int i = 0; i < m; i++) gv[i] = st_f(prec, gamf * (float)z[i]);
         if (pointwise && p->kind == ORC_K_C2D5) {
-            float ar = g.Sf.d, ai = g.Sf.e, den = ar * ar + ai * ai;
             for (int i = 0; i < m / 2; i++) {
+                float ar = g.Sf.d, ai = g.Sf.ep ? g.Sf.ep[i] : g.Sf.e, den = ar * ar + ai * ai;
                 float gr = gv[2 * i], gi = gv[2 * i + 1];
                 yf[2 * i] = st_f(prec, (gr * ar + gi * ai) / den);
                 yf[2 * i + 1] = st_f(prec, (gi * ar - gr * ai) / den);
@@ -710,7 +741,8 @@ double orc_residual_dd(const orc_problem *p, int prec, const double *b, const do
                             dd_sub(&hi, &lo, A->c[dir], j >= 0 ? x_out[K * j + part] : 0.0);
                         }
                         /* (i e) (xr + i xi) = -e xi + i e xr */
-                        if (cplx) dd_sub(&hi, &lo, part ? A->e : -A->e, x_out[K * i + (1 - part)]);
+                        double ei = A->ep ? A->ep[i] : A->e;
+                        if (cplx) dd_sub(&hi, &lo, part ? ei : -ei, x_out[K * i + (1 - part)]);
                         ef_sum(hi, lo, &r_hi[ii], &r_lo[ii]);
                     }
                 }
@@ -734,7 +766,9 @@ void orc_apply(const orc_problem *p, int which, const double *x, double *y)
     }
     double co[8];
     orc_stencil_coeffs(p->kind, which, p->h, p->beta, p->kappa, p->sigma, co);
-    orc_stencil_apply(p->kind, p->nx, p->ny, p->nz, co, x, y);
+    orc_op op = make_stencil_op(p->kind, p->nx, p->ny, p->nz, co);
+    if (p->kind == ORC_K_C2D5 && p->sigma_pt && which != OP_M) op.ep = p->sigma_pt;
+    apply_d(&op, x, y);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -40,7 +40,7 @@ class Problem(C.Structure):
     _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("h", C.c_double), ("beta", C.c_double * 3), ("kappa", C.c_double),
                 ("sigma", C.c_double), ("n", C.c_int), ("rowptr", C.c_void_p),
-                ("col", C.c_void_p), ("val", C.c_void_p)]
+                ("col", C.c_void_p), ("val", C.c_void_p), ("sigma_pt", C.c_void_p)]
 
 
 class Opts(C.Structure):
@@ -164,7 +164,7 @@ class Gadi:
     """One linear system: a handle of the C ABI (gadi_create / gadi_destroy)."""
 
     def __init__(self, kind, nx=0, ny=1, nz=1, h=0.0, beta=(0.0, 0.0, 0.0), kappa=0.0,
-                 sigma=0.0, rowptr=None, col=None, val=None):
+                 sigma=0.0, rowptr=None, col=None, val=None, sigma_pt=None):
         import numpy as np
         P = Problem()
         P.kind, P.nx, P.ny, P.nz, P.h = int(kind), int(nx), int(ny), int(nz), float(h)
@@ -182,6 +182,10 @@ class Gadi:
         else:
             n = int(nx) * int(ny) * (int(nz) if kind == STENCIL_3D7 else 1)
             self.nvec = 2 * n if kind == COMPLEX_2D5 else n
+            if sigma_pt is not None:
+                sg = np.ascontiguousarray(sigma_pt, np.float64)
+                self._keep = [sg]
+                P.sigma_pt = sg.ctypes.data
         self.kind = kind
         h_ = C.c_void_p()
         st = lib().gadi_create(C.byref(P), SPLIT_HSS, C.byref(h_))
@@ -192,7 +196,8 @@ class Gadi:
     @classmethod
     def from_problem(cls, p):
         """From a workloads.Problem descriptor."""
-        return cls(p.kind, p.nx, p.ny, p.nz, p.h, p.beta, p.kappa, p.sigma, p.rowptr, p.col, p.val)
+        return cls(p.kind, p.nx, p.ny, p.nz, p.h, p.beta, p.kappa, p.sigma, p.rowptr, p.col, p.val,
+                   getattr(p, "sigma_pt", None))
 
     def close(self):
         if getattr(self, "h", None):
@@ -302,6 +307,12 @@ def _problem_struct(p):
     P.kind, P.nx, P.ny, P.nz, P.h = int(p.kind), int(p.nx), int(p.ny), int(p.nz), float(p.h)
     P.beta = (C.c_double * 3)(*[float(x) for x in p.beta])
     P.kappa, P.sigma = float(p.kappa), float(p.sigma)
+    sig = getattr(p, "sigma_pt", None)
+    if sig is not None:
+        import numpy as np
+        sg = np.ascontiguousarray(sig, np.float64)
+        P._sig = sg  # keep alive with the struct
+        P.sigma_pt = sg.ctypes.data
     return P
 
 

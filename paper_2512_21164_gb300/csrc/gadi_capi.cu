@@ -98,6 +98,7 @@ struct gadi_handle {
     int *d_abort = nullptr, *d_flag = nullptr, *h_flag = nullptr;
     double *d_stage = nullptr; // 2 * nelem doubles for host b / x
     double *d_pw = nullptr;    // power-iteration vectors (3 * nelem)
+    double *d_sig = nullptr;   // complex class: per-point T (npts), or null
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -378,6 +379,8 @@ void fill_base(gadi_handle *h, Params &P, int prec)
 {
     std::memset(&P, 0, sizeof P);
     P.kind = h->kind;
+    P.sig = h->d_sig;
+    P.sig_a = 1.0;
     P.prec = prec;
     P.nx = h->nx;
     P.ny = h->ny;
@@ -523,6 +526,9 @@ gadi_status apply_dev(gadi_handle *h, gadi_op op, const double *x, double *y, cu
     } else {
         const Stencil &M = h->M, &N = h->N;
         Stencil s{};
+        // a per-point T enters A and N with +, A^T with -, M not at all
+        P.sig_a = op == GADI_OP_AT ? -1.0 : 1.0;
+        if (op == GADI_OP_M) P.sig = nullptr;
         if (op == GADI_OP_A) s = h->A;
         else if (op == GADI_OP_M) s = M;
         else if (op == GADI_OP_N) s = N;
@@ -634,6 +640,16 @@ gadi_status gadi_create(const gadi_problem *p, gadi_splitting split, gadi_handle
             h->sigma = p->sigma;
             stencil_coefs(h);
         }
+        if (st == GADI_OK && p->kind == GADI_COMPLEX_2D5 && p->sigma_pt) {
+            for (long long i = 0; i < h->npts; i++)
+                if (!std::isfinite(p->sigma_pt[i])) st = GADI_ERR_NONFINITE;
+            if (st == GADI_OK) {
+                const size_t bytes = sizeof(double) * (size_t)h->npts;
+                if (cudaMalloc(&h->d_sig, bytes) != cudaSuccess) st = GADI_ERR_OOM;
+                else if (cudaMemcpy(h->d_sig, p->sigma_pt, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+                    st = GADI_ERR_CUDA;
+            }
+        }
     } else {
         const int n = p->n;
         if (n <= 0 || !p->rowptr || !p->col || !p->val) st = GADI_ERR_INVALID;
@@ -720,7 +736,7 @@ void gadi_destroy(gadi_handle *h)
     if (!h) return;
     void *dev[] = {h->d_rowptr, h->d_col, h->d_mrowptr, h->d_mcol, h->d_aval, h->d_mval, h->d_nval,
                    h->d_atval, h->d_opval, h->d_ws, h->d_part, h->d_hist, h->d_ctl, h->d_bar,
-                   h->d_abort, h->d_flag, h->d_stage, h->d_pw};
+                   h->d_abort, h->d_flag, h->d_stage, h->d_pw, h->d_sig};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -838,7 +854,13 @@ bool stencil_spectra(const gadi_problem *p, double *lmin, double *lmax, double *
     }
     lo += p->kappa;
     hi += p->kappa;
-    if (p->kind == GADI_COMPLEX_2D5) nn = std::fabs(p->sigma);
+    if (p->kind == GADI_COMPLEX_2D5) {
+        nn = std::fabs(p->sigma);
+        if (p->sigma_pt) {
+            nn = 0.0;
+            for (long long i = 0; i < (long long)p->nx * p->ny; i++) nn = std::max(nn, std::fabs(p->sigma_pt[i]));
+        }
+    }
     *lmin = lo;
     *lmax = hi;
     *nnorm = nn;

@@ -103,6 +103,22 @@ template <class C> struct Coef7 {
     C d, c[6], e;
 };
 
+// The complex class's imaginary diagonal at element v of the chunk that
+// starts at element g (two elements per grid point): the scalar e of the
+// coefficient set, or sign * T_i for a per-point T (`sig`, FP64) -- exact in
+// the FP64 phases, rounded to u_s in the inner ones, as stored coefficients.
+__device__ __forceinline__ double pt_e_exact(const double *sig, double sign, long long g, int v, double e)
+{
+    return sig ? sign * __ldg(sig + ((g + v) >> 1)) : e;
+}
+template <int PREC>
+__device__ __forceinline__ typename Prec<PREC>::C pt_e_us(const double *sig, typename Prec<PREC>::C sign,
+                                                          long long g, int v, typename Prec<PREC>::C e)
+{
+    using PT = Prec<PREC>;
+    return sig ? sign * PT::ld(PT::from_f64(__ldg(sig + ((g + v) >> 1)))) : e;
+}
+
 // ---------------------------------------------------------------------------
 // fields: the stencil input of a phase, computed from raw loads
 // ---------------------------------------------------------------------------
@@ -553,6 +569,8 @@ struct PhResidual {
     S *rs;
     Coef7<double> cf;
     double *rlo; // DD: low parts of r (nullable)
+    const double *sig = nullptr; // complex class: per-point T (null: cf.e)
+    double esign = 1.0;
     __device__ void load_own(long long g, Own &o) const
     {
         if (b) VecIO<double, W>::load(b + g, o.v[0]);
@@ -576,15 +594,19 @@ struct PhResidual {
                     dd_sub_term(hi, lo, cf.c[4], bb[v]);
                     dd_sub_term(hi, lo, cf.c[5], t[v]);
                 }
-                if constexpr (K == 2) dd_sub_term(hi, lo, (v & 1) ? cf.e : -cf.e, c[v ^ 1]);
+                if constexpr (K == 2) {
+                    const double ev = pt_e_exact(sig, esign, g, v, cf.e);
+                    dd_sub_term(hi, lo, (v & 1) ? ev : -ev, c[v ^ 1]);
+                }
                 two_sum(hi, lo, r[v], rl[v]);
             }
         } else {
             double ax[W];
 #pragma unroll
             for (int v = 0; v < W; v++)
-                ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c, cf.e, c[v], w[v], e[v], s[v], n[v],
-                                                          bb[v], t[v], c[v ^ (K - 1)], (v & 1) != 0);
+                ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c, K == 2 ? pt_e_exact(sig, esign, g, v, cf.e) : 0.0,
+                                                          c[v], w[v], e[v], s[v], n[v], bb[v], t[v], c[v ^ (K - 1)],
+                                                          (v & 1) != 0);
             if (b == nullptr) { // operator application: xo = Op x
                 VecIO<double, W>::store(xo + g, ax);
                 return;
@@ -719,6 +741,7 @@ struct PhS0 {
     Fld f;
     S *t;
     Coef7<C> st;
+    const double *sig = nullptr; // complex class: per-point T (null: st.e)
     __device__ void load_own(long long, Own &) const {}
     static constexpr int NO = 0;
     __device__ const S *own_vec(int) const { return nullptr; }
@@ -731,7 +754,7 @@ struct PhS0 {
         S to[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
+            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, K == 2 ? pt_e_us<PREC>(sig, C(-1), g, v, st.e) : C(0), c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
                                                      c[v ^ (K - 1)], (v & 1) != 0);
             to[v] = PT::st(q);
             const C qq = PT::ld(to[v]);
@@ -753,6 +776,7 @@ struct PhS1 {
     Fld f;
     S *pnew, *u;
     Coef7<C> sc;
+    const double *sig = nullptr; // complex class: per-point T (null: sc.e)
     __device__ void load_own(long long, Own &) const {}
     static constexpr int NO = 0;
     __device__ const S *own_vec(int) const { return nullptr; }
@@ -765,7 +789,7 @@ struct PhS1 {
         S ps[W], us[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, K == 2>(sc.d, sc.c, sc.e, c[v], w[v], e[v], s[v], n[v], b[v], t[v],
+            const C q = stencil_at<A, C, D3, K == 2>(sc.d, sc.c, K == 2 ? pt_e_us<PREC>(sig, C(+1), g, v, sc.e) : C(0), c[v], w[v], e[v], s[v], n[v], b[v], t[v],
                                                      c[v ^ (K - 1)], (v & 1) != 0);
             us[v] = PT::st(q);
             const C uu = PT::ld(us[v]);
@@ -792,6 +816,7 @@ struct PhS2 {
     C a;
     bool first;
     Coef7<C> st;
+    const double *sig = nullptr; // complex class: per-point T (null: st.e)
     __device__ void load_own(long long g, Own &o) const
     {
         VecIO<S, W>::load(p + g, o.v[0]);
@@ -817,7 +842,7 @@ struct PhS2 {
         S yv[W], tv[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
-            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, st.e, c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
+            const C q = stencil_at<A, C, D3, K == 2>(st.d, st.c, K == 2 ? pt_e_us<PREC>(sig, C(-1), g, v, st.e) : C(0), c[v], w[v], e[v], s[v], n[v], b[v], tt[v],
                                                      c[v ^ (K - 1)], (v & 1) != 0);
             const C pp = PT::ld(o.v[0][v]);
             yv[v] = PT::st(first ? A::mul(a, pp) : A::madd(a, pp, PT::ld(o.v[1][v])));
@@ -890,14 +915,14 @@ struct StencilImpl {
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
         double a[2] = {0.0, 0.0}; // a[1]: the float pair (hi, lo), both +0
-        PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out};
+        PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out, P.sig, P.sig_a};
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
         acc[1] = (double)__int_as_float(__double2hiint(a[1])) + (double)__int_as_float(__double2loint(a[1]));
     }
     __device__ void apply(const double *x, double *yout) const
     {
-        PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca};
+        PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca, nullptr, P.sig, P.sig_a};
         double a[2] = {0.0, 0.0};
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
     }
@@ -945,21 +970,21 @@ struct StencilImpl {
     __device__ void s0(C gamma, AT (&acc)[2]) const
     {
         PhS0<PREC, WI, K, D3> ph;
-        ph.f.src = (const S *)P.z; ph.f.scale = gamma; ph.t = (S *)P.r; ph.st = ct;
+        ph.f.src = (const S *)P.z; ph.f.scale = gamma; ph.t = (S *)P.r; ph.st = ct; ph.sig = P.sig;
         sweep(ph, acc);
     }
     __device__ void s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
         PhS1<PREC, WI, K, D3> ph;
         ph.f.src = (const S *)P.r; ph.f.pold = pold; ph.f.beta = beta; ph.f.first = first;
-        ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs;
+        ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs; ph.sig = P.sig;
         sweep(ph, acc);
     }
     __device__ void s2(bool first, C a_, const S *p, AT (&acc)[2]) const
     {
         PhS2<PREC, WI, K, D3> ph;
         ph.f.src = (const S *)P.u; ph.f.scale = C(1); ph.p = p; ph.y = (S *)P.y; ph.t = (S *)P.r;
-        ph.a = a_; ph.first = first; ph.st = ct;
+        ph.a = a_; ph.first = first; ph.st = ct; ph.sig = P.sig;
         sweep(ph, acc);
     }
     // ---- SM-resident H-solve (2D real class, FP32/BF16, 16-byte chunks) ----
@@ -1204,17 +1229,21 @@ struct StencilImpl {
         }
     }
 
-    // complex class: S = (alpha + i sigma) I, y = fl_s(g / (alpha + i sigma))
+    // complex class: S = alpha I + i T (T = sigma I or diag(T_i)),
+    // y = fl_s(g / (alpha + i T_i)) pointwise
     __device__ void s_pointwise(C gamma) const
     {
         if constexpr (K == 2) {
             using AE = ArExact<C>;
-            const C ar = cs.d, ai = cs.e;
-            const C den = AE::add(AE::mul(ar, ar), AE::mul(ai, ai));
+            const C ar = cs.d;
+            const C den0 = AE::add(AE::mul(ar, ar), AE::mul(cs.e, cs.e));
             const S *z = (const S *)P.z;
             S *y = (S *)P.y;
             const long long np = (long long)P.nx * ny;
             for (long long i = vg.tid(); i < np; i += vg.nthreads()) {
+                // a per-point T_i is rounded to u_s, as a stored coefficient
+                const C ai = P.sig ? PT::ld(PT::from_f64(__ldg(P.sig + i))) : cs.e;
+                const C den = P.sig ? AE::add(AE::mul(ar, ar), AE::mul(ai, ai)) : den0;
                 const C gr = PT::ld(PT::st(A::mul(gamma, PT::ld(z[2 * i]))));
                 const C gi = PT::ld(PT::st(A::mul(gamma, PT::ld(z[2 * i + 1]))));
                 const C yr = AE::div(AE::add(AE::mul(gr, ar), AE::mul(gi, ai)), den);

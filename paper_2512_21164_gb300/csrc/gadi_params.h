@@ -69,6 +69,11 @@ struct Params {
     int maxit, maxit_inner, inner_stag, outer_win, pointwise, first_y_null;
     int resident;  // 1: the H-solve keeps p in shared memory (2D, FP32/BF16)
     int ur_dd;     // 1: the residual in double-FP64 (u_r ~ u^2)
+    // complex class with a per-point imaginary diagonal T = diag(sig) (FP64,
+    // one value per grid point; null: the scalar sigma of the coefficients);
+    // sig_a: the sign T carries in the FP64 set `a` (A, N: +1, A^T: -1, M: 0)
+    const double *sig;
+    double sig_a;
     double *part;  // 2 slots x 2 values x gridDim doubles
     double *hist;  // maxit + 1 doubles (device)
     Ctl *ctl;

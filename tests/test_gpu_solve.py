@@ -289,3 +289,20 @@ def test_paper_2d_instance_matches_oracle(prec):
     assert so["status"] == "OK" and st == G.OK, G.status_str(st)
     assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
     assert np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+def test_paper_complex_instance_matches_oracle(prec):
+    """Sec. 5.4's own instance (random per-point potential) at 48 x 48 against
+    the oracle: pointwise S-solve with the per-point diagonal."""
+    from workloads import paper_complex_rd
+    p, xt = paper_complex_rd(48)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    a = 64 * alpha_star(p)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, a, 1.0, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts, s_pointwise=True)
+    st, sg, xg, hg = _gpu_solve(p, b, a, 1.0, prec, 1e-10, 3000)
+    assert so["status"] == "OK" and st == G.OK, G.status_str(st)
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+    assert np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b) <= 1e-10

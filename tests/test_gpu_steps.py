@@ -15,7 +15,8 @@ import pytest
 import oracle as O
 import paper_2512_21164_gb300 as G
 from helpers import BF16, FP32, FP64, PRECS, dev64, us_empty, us_to_device, us_to_host
-from workloads import K_3D7, Problem, SplitMix64, complex_rd, conv_diff_2d, conv_diff_3d, random_csr
+from workloads import (K_3D7, Problem, SplitMix64, complex_rd, conv_diff_2d, conv_diff_3d, paper_complex_rd,
+                       random_csr)
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +36,8 @@ CASES = {
                           SplitMix64(111).uniform_array(7 * 5 * 9)),
     "cplx_vec": lambda: complex_rd(32, 107),
     "cplx_odd": lambda: complex_rd(13, 108),
+    # per-point imaginary diagonal (the random potential of Sec. 5.4)
+    "cplx_pt": lambda: paper_complex_rd(32, 115),
     "csr": lambda: random_csr(300, 109),
 }
 
@@ -184,7 +187,7 @@ def test_solve_s_fixed_iterations(case, prec):
         assert err <= FIXED_TOL[prec] * its, (its, err)
 
 
-@pytest.mark.parametrize("case", ["cplx_vec", "cplx_odd"])
+@pytest.mark.parametrize("case", ["cplx_vec", "cplx_odd", "cplx_pt"])
 @pytest.mark.parametrize("prec", PRECS)
 def test_solve_s_pointwise_bit_exact(case, prec):
     p, xt = CASES[case]()

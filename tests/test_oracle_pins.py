@@ -481,3 +481,53 @@ def test_reaction_term_shifts_the_spectrum():
     d0, d1 = O.Oracle(p0).dense(O.OP_M), O.Oracle(p1).dense(O.OP_M)
     assert np.allclose(d1 - d0, 0.75 * np.eye(20), rtol=0, atol=1e-15)
     assert np.array_equal(O.Oracle(p1).dense(O.OP_N), O.Oracle(p0).dense(O.OP_N))
+
+
+def test_paper_complex_instance_equals_printed_form():
+    """Sec. 5.4's system -nu Lap w + i V w = f: (nu/h^2) G + i diag(V) with G
+    the 5-point graph Laplacian, V = s U[0,1) per point, nu = 1e-5 (64/n)^2.
+    The workload is that matrix times h^2/nu; its real block form [[L, -V],
+    [V, L]] (interleaved here) has M = L symmetric and N skew."""
+    from workloads import paper_complex_rd
+    n = 6
+    p, w1 = paper_complex_rd(n, seed=9)
+    h = 1.0 / (n + 1)
+    nu = 1e-5 * (64.0 / n) ** 2
+    V = 1e4 * SplitMix64(9).uniform_array(n * n)
+    G = np.kron(np.eye(n), _tri(n, -1, 2, -1)) + np.kron(_tri(n, -1, 2, -1), np.eye(n))
+    Ap = (nu / h ** 2) * G + 1j * np.diag(V)
+    orc = O.Oracle(p)
+    g = SplitMix64(10)
+    x = g.uniform_array(2 * n * n) - 0.5
+    xc = x[0::2] + 1j * x[1::2]
+    y = orc.apply(O.OP_A, x)
+    yc = (h ** 2 / nu) * (Ap @ xc)
+    scale = np.max(np.abs(yc))
+    assert np.allclose(y[0::2], yc.real, rtol=0, atol=1e-13 * scale)
+    assert np.allclose(y[1::2], yc.imag, rtol=0, atol=1e-13 * scale)
+    M, N = orc.dense(O.OP_M), orc.dense(O.OP_N)
+    assert np.array_equal(M, M.T) and np.array_equal(N, -N.T)
+    assert np.array_equal(M + N, orc.dense(O.OP_A))
+    assert np.array_equal(w1, np.ones(2 * n * n))
+
+
+@pytest.mark.parametrize("prec", [O.FP64, O.FP32, O.BF16])
+def test_pointwise_s_solve_per_point_diagonal(prec):
+    """S = alpha I + i diag(T_i): the pointwise solve equals the exact complex
+    division by (alpha + i fl_s(T_i)), point by point, up to u_s."""
+    from workloads import paper_complex_rd
+    p, _ = paper_complex_rd(5, seed=11)
+    orc = O.Oracle(p)
+    g = SplitMix64(12)
+    z = np.array([O.round_prec(prec, v) for v in g.uniform_array(2 * p.npoints) - 0.5])
+    alpha, omega = 3.0, 0.5
+    y, its = orc.solve_s(alpha, omega, prec, z, 1e-3, 100, 10, pointwise=True)
+    assert its == 1
+    gam = (2 - omega) * alpha
+    T = np.array([O.round_prec(prec, t) for t in p.sigma_pt])
+    a = O.round_prec(prec, alpha)
+    zc = z[0::2] + 1j * z[1::2]
+    want = np.array([O.round_prec(prec, O.round_prec(prec, gam) * v) for v in z])
+    want = (want[0::2] + 1j * want[1::2]) / (a + 1j * T)
+    u = {O.FP64: 2.0 ** -52, O.FP32: 2.0 ** -23, O.BF16: 2.0 ** -7}[prec]
+    assert np.allclose(y[0::2] + 1j * y[1::2], want, rtol=0, atol=8 * u * np.max(np.abs(want)))

@@ -75,6 +75,9 @@ class Problem:
     rowptr: np.ndarray | None = None
     col: np.ndarray | None = None
     val: np.ndarray | None = None
+    # complex class: a per-point imaginary diagonal T_i (nx*ny values) instead
+    # of sigma I
+    sigma_pt: np.ndarray | None = None
     name: str = ""
     meta: dict = field(default_factory=dict)
 
@@ -191,6 +194,26 @@ def paper_cd_3d(n: int) -> tuple[Problem, np.ndarray]:
     the printed diagonal); b from x = (1, ..., 1)."""
     p = Problem(K_3D7, n, n, n, 1.0 / (n + 1), (1.0, 1.0, 1.0), name=f"paper 3D CD {n}^3")
     return p, np.ones(n * n * n)
+
+
+def paper_complex_rd(n: int, seed: int = 6, s: float = 1e4) -> tuple[Problem, np.ndarray]:
+    """The complex reaction-diffusion instance of Sec. 5.4 on n x n:
+    -nu Lap w + i V(x) w = f, V = s U[0,1) per grid point (drawn by grid
+    index), s = 1e4, nu = 1e-5 (64/n)^2, h = 1/(n+1).  Reading: L is nu times
+    the 1/h^2-scaled 5-point Laplacian (the nu ~ 1/n^2 scaling then keeps
+    nu/h^2, hence the difficulty, about constant in n).  Multiplying the
+    system by h^2/nu gives this module's complex class exactly: M = the
+    5-point graph Laplacian (kappa = 0), T_i = (h^2/nu) V_i per point; the
+    solution, relative residuals and GADI's iterates (with alpha scaled by
+    the same factor) are those of the unscaled system.  b from w = 1 + i at
+    every point (Sec. 5.3's recipe; Sec. 5.4 names none)."""
+    h = 1.0 / (n + 1)
+    nu = 1e-5 * (64.0 / n) ** 2
+    g = SplitMix64(seed)
+    V = s * g.uniform_array(n * n)
+    p = Problem(K_C2D5, n, n, 1, h, (0.0, 0.0, 0.0), 0.0, 0.0, sigma_pt=(h * h / nu) * V,
+                name=f"paper complex RD {n}x{n}")
+    return p, np.ones(2 * n * n)
 
 
 def alpha_star(p: Problem) -> float:
