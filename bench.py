@@ -418,6 +418,38 @@ def run_paper(args):
         H.close()
 
 
+def run_c2_dd(args):
+    """The headline workload (2048^2, FP32 inner, alpha = 8 alpha*, omega = 0,
+    tolerance 1e-10) with the residual in double-FP64 (u_r ~ u^2) beside the
+    default FP64 residual: time, iterations, relres and forward error."""
+    import torch
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import alpha_star, config2
+    B.build()
+    p, xt = config2(args.grid)
+    H = G.Gadi.from_problem(p)
+    xtd = torch.from_numpy(xt).cuda()
+    b = torch.zeros_like(xtd)
+    H.apply(G.OP_A, xtd, b)
+    x = torch.zeros_like(b)
+    alpha = ALPHA_FACTOR * alpha_star(p)
+    for ur, name in ((G.FP64, "fp64"), (G.FP64X2, "double-fp64")):
+        x.zero_()
+        H.solve(b, x, alpha, OMEGA, G.FP32, TOL, 3, tol_h=TOL_H, tol_s=TOL_S, u_r=ur)  # warm-up
+        x.zero_()
+        st, s = H.solve(b, x, alpha, OMEGA, G.FP32, TOL, args.maxit, tol_h=TOL_H, tol_s=TOL_S, u_r=ur)
+        fe = float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))
+        print(json.dumps({
+            "metric": "time to 1e-10 relative residual with residual precision u_r", "workload": "c2dd",
+            "config": {"workload": WORKLOAD, "alpha_over_alpha_star": ALPHA_FACTOR, "omega": OMEGA,
+                       "u_s": "fp32", "u_r": name},
+            "value": s["seconds"], "unit": "s", "status": G.status_str(st), "outer_its": s["outer_its"],
+            "inner_its_h": s["inner_its_h"], "inner_its_s": s["inner_its_s"], "relres": s["relres"],
+            "forward_error": fe, "ms_per_outer": 1e3 * s["seconds"] / max(1, s["outer_its"])}), flush=True)
+
+
 def run_workload(args):
     """Time-to-tolerance of one configuration for each precision (one solve
     each after a capped warm-up), with the same roofline accounting as the
@@ -591,7 +623,8 @@ def main():
     ap.add_argument("--precs", default="fp64,fp32,bf16", help="paper2d / paper3d / paperc: inner precisions")
     ap.add_argument("--alpha-factors", default=None,
                     help="paper2d / paper3d: alpha/alpha*:omega pairs tried (default 2:0,4:0,8:0 / 0.1:1,0.3:1,1:0)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper2d", "paper3d", "paperc"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc"],
                     help="c2 (default): the headline line; others: per-precision lines")
     ap.add_argument("--grid3", type=int, default=512)
     ap.add_argument("--grid4", type=int, default=4096)
@@ -609,6 +642,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "c5" and args.impl == "ours":
         run_batched(args)
+    elif args.workload == "c2dd" and args.impl == "ours":
+        run_c2_dd(args)
     elif args.workload in ("paper2d", "paper3d", "paperc") and args.impl == "ours":
         run_paper(args)
     elif args.workload != "c2" and args.impl == "ours":

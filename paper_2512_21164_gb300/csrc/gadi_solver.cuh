@@ -337,14 +337,15 @@ struct Runner {
         for (int j = 0; j < P.maxit_inner; ++j) {
             S *pnew = (S *)((j & 1) ? P.p1 : P.p0);
             const S *pold = (const S *)((j & 1) ? P.p0 : P.p1);
-            if (Impl::RESIDENT && P.resident) {
+            // the resident instantiation runs only with P.resident set
+            if constexpr (Impl::RESIDENT) {
                 I.h1r(j, beta, acc);
             } else if (!I.h1(j == 0, beta, pold, pnew, acc, gs)) {
                 return -1;
             }
             if (!reduce(acc, sum)) return -1;
             const C a = A::div(rr, (C)sum[0]);
-            if (Impl::RESIDENT && P.resident) {
+            if constexpr (Impl::RESIDENT) {
                 I.h2r(j == 0, a, acc);
             } else if (!I.h2(j == 0, a, pnew, acc, gs)) {
                 return -1;
