@@ -248,9 +248,15 @@ struct StencilAdapter {
         si.apply(x, yout);
         return true;
     }
-    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &) const
+    __device__ bool h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &gs) const
     {
-        si.h1(first, beta, pold, pnew, acc);
+        if constexpr (SI::SPLIT_P) {
+            si.p_update(first, beta, pold, pnew);
+            if (!gs.sync()) return false;
+            si.h1_split(pnew, acc);
+        } else {
+            si.h1(first, beta, pold, pnew, acc);
+        }
         return true;
     }
     __device__ bool h2(bool first, C a, const S *p, AT (&acc)[2], const GridSync &) const
@@ -263,9 +269,15 @@ struct StencilAdapter {
         si.s0(gamma, acc);
         return true;
     }
-    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &) const
+    __device__ bool s1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &gs) const
     {
-        si.s1(first, beta, pold, pnew, acc);
+        if constexpr (SI::SPLIT_P) {
+            si.p_update(first, beta, pold, pnew);
+            if (!gs.sync()) return false;
+            si.s1_split(pnew, acc);
+        } else {
+            si.s1(first, beta, pold, pnew, acc);
+        }
         return true;
     }
     __device__ bool s2(bool first, C a, const S *p, AT (&acc)[2], const GridSync &) const
