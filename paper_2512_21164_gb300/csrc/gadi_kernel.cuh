@@ -732,7 +732,7 @@ struct PhH2 {
 // p.(H p) with p already stored (the 3D form of H1: a pointwise p update
 // first, so the stencil pass reads p instead of recomputing it from r and
 // p_old at every neighbour row)
-template <int PREC, int W, int K, bool D3>
+template <int PREC, int W, int K, bool D3, bool STORE_Q = false>
 struct PhPHp {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -742,21 +742,25 @@ struct PhPHp {
     using Own = OwnIn<S, W, 0>;
     Fld f;
     Coef7<C> h;
+    S *qout; // STORE_Q: H p written out for a pointwise H2
     __device__ void load_own(long long, Own &) const {}
     static constexpr int NO = 0;
     __device__ const S *own_vec(int) const { return nullptr; }
     __device__ bool own_used(int) const { return false; }
     __device__ void own_from_smem(const S *const *, Own &) const {}
     template <class AT>
-    __device__ void out(long long, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
+    __device__ void out(long long g, const Own &, const C (&c)[W], const C (&w)[W], const C (&e)[W],
                         const C (&s)[W], const C (&n)[W], const C (&b)[W], const C (&t)[W], AT (&acc)[2]) const
     {
+        S qs[W];
 #pragma unroll
         for (int v = 0; v < W; v++) {
             const C q = stencil_at<A, C, D3, false>(h.d, h.c, C(0), c[v], w[v], e[v], s[v], n[v], b[v], t[v],
                                                     C(0), false);
             acc[0] += (AT)c[v] * (AT)q;
+            qs[v] = PT::st(q);
         }
+        if constexpr (STORE_Q) VecIO<S, W>::store(qout + g, qs);
     }
 };
 
@@ -1047,13 +1051,13 @@ struct StencilImpl {
         ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs; ph.sig = P.sig;
         sweep(ph, acc);
     }
-    // 3D BF16: the direction update p = fl_s(src + beta p_old) (p = src at
-    // first) as its own pointwise pass (src = P.r: the CG residual r or the
-    // CGNR residual t), then the stencil pass on the stored p.  Measured at
-    // 512^3: 6 % faster per outer iteration for BF16, slower for FP32 (whose
-    // fused pass recomputes p at the neighbour rows more cheaply than an
-    // extra pass over memory costs).
-    static constexpr bool SPLIT_P = D3 && PREC == P_BF16;
+    // 3D BF16 and FP64: the direction update p = fl_s(src + beta p_old) (p =
+    // src at first) as its own pointwise pass (src = P.r: the CG residual r
+    // or the CGNR residual t), then the stencil pass on the stored p.
+    // Measured at 512^3 / 320^3: 5-6 % faster per outer iteration for BF16
+    // and FP64, slower for FP32 (whose fused pass recomputes p at the
+    // neighbour rows more cheaply than an extra pass over memory costs).
+    static constexpr bool SPLIT_P = D3 && (PREC == P_BF16 || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
         using A2 = typename InnerAr<PREC>::T;
@@ -1072,8 +1076,8 @@ struct StencilImpl {
     }
     __device__ void h1_split(const S *p, AT (&acc)[2]) const
     {
-        PhPHp<PREC, WI, K, D3> ph;
-        ph.f.src = p; ph.f.scale = C(1); ph.h = ch;
+        PhPHp<PREC, WI, K, D3, STORE_Q> ph;
+        ph.f.src = p; ph.f.scale = C(1); ph.h = ch; ph.qout = (S *)P.u;
         sweep(ph, acc);
     }
     __device__ void s1_split(const S *p, AT (&acc)[2]) const
