@@ -378,7 +378,18 @@ def run_paper(args):
         {"paper2d": [960, 2560, 4096], "paper3d": [180, 256, 320], "paperc": [1024, 2048, 4096]}[w]
     spec = args.alpha_factors or {"paper2d": "4:0,8:0,16:0", "paper3d": "0.05:1,0.1:1,0.3:1",
                                   "paperc": "64:1,256:1,1024:1"}[w]
-    factors = [(float(v.split(":")[0]), float(v.split(":")[1]) if ":" in v else 0.0) for v in spec.split(",")]
+    gpr = spec.startswith("gpr")
+    if gpr:
+        # Sec. 4.2: alpha predicted by a GPR trained on small instances of the
+        # family (sizes below), omega as given after the colon (default 0)
+        omega_g = float(spec.split(":")[1]) if ":" in spec else 0.0
+        train_sizes = {"paper2d": [64, 96, 128, 192], "paper3d": [24, 32, 48, 64],
+                       "paperc": [64, 96, 128, 192]}[w]
+        from paper_2512_21164_gb300 import alpha_gpr
+        models = {}
+        factors = []
+    else:
+        factors = [(float(v.split(":")[0]), float(v.split(":")[1]) if ":" in v else 0.0) for v in spec.split(",")]
     tol = 1e-10 if w == "paper2d" else 1e-6
     table = {"paper2d": PAPER_TABLE2, "paper3d": PAPER_TABLE3, "paperc": PAPER_TABLE4}[w]
     section = {"paper2d": "2D CDR (Sec. 5.2)", "paper3d": "3D CD (Sec. 5.3)", "paperc": "complex RD (Sec. 5.4)"}[w]
@@ -396,6 +407,15 @@ def run_paper(args):
             prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[pn]
             tin = 1e-2 if pn == "bf16" else TOL_INNER
             runs = []
+            gpr_note = None
+            if gpr:
+                if pn not in models:
+                    fam = {"paper2d": paper_cdr_2d, "paper3d": paper_cd_3d, "paperc": paper_complex_rd}[w]
+                    models[pn] = alpha_gpr.train(fam, train_sizes, prec, omega_g, tol, alpha_star)
+                fl, fs = models[pn].predict_log2_factor(n)
+                factors = [(2.0 ** fl, omega_g)]
+                gpr_note = {"log2_factor": fl, "std": fs, "train_sizes": train_sizes,
+                            "train_best_log2": [float(v) for v in models[pn].gp.predict(models[pn].gp.x)[0]]}
             for f, om in factors:
                 x.zero_()
                 H.solve(b, x, f * a0, om, prec, tol, 3, tol_h=tin, tol_s=tin)  # warm-up
@@ -413,7 +433,7 @@ def run_paper(args):
                 "outer_its": s["outer_its"], "inner_its_h": s["inner_its_h"], "inner_its_s": s["inner_its_s"],
                 "restarts": s["restarts"], "relres": s["relres"], "forward_error": fe,
                 "sweep": [{"f": r[2][0], "omega": r[2][1], "s": r[1], "status": G.status_str(r[3]),
-                           "outer": r[4]["outer_its"]} for r in runs],
+                           "outer": r[4]["outer_its"]} for r in runs], "gpr": gpr_note,
                 "paper_a100_s": table.get(n, (None, None, None))[j]}), flush=True)
         H.close()
 
@@ -620,7 +640,8 @@ def main():
     ap.add_argument("--grids", default=None, help="paper2d / paper3d / paperc: comma-separated grid sizes")
     ap.add_argument("--precs", default="fp64,fp32,bf16", help="paper2d / paper3d / paperc: inner precisions")
     ap.add_argument("--alpha-factors", default=None,
-                    help="paper2d / paper3d: alpha/alpha*:omega pairs tried (default 2:0,4:0,8:0 / 0.1:1,0.3:1,1:0)")
+                    help="paper2d / paper3d / paperc: alpha/alpha*:omega pairs tried, or gpr[:omega] for the "
+                         "alpha of a GPR trained on small instances (Sec. 4.2)")
     ap.add_argument("--workload", default="c2",
                     choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc"],
                     help="c2 (default): the headline line; others: per-precision lines")
