@@ -75,3 +75,43 @@ def test_batched_rejects_other_classes():
         x = torch.zeros_like(b)
         st, _ = G.solve_batched([H], 1, [b], [x], [1.0], check=False)
     assert st == G.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_batched_double_fp64_residual_matches_single(prec):
+    """The batched kernel with the residual in double-FP64 (u_r ~ u^2): every
+    unit converges and its iterate satisfies the tolerance by the oracle's
+    double-FP64 residual, with outer iterations in the band of the single
+    double-FP64 solve of the same system."""
+    import torch
+    nrhs = 2
+    systems = _systems()[:3]
+    g = SplitMix64(78)
+    handles, bs, xs, alphas, rhs = [], [], [], [], []
+    for p, a in systems:
+        orc = O.Oracle(p)
+        bb = np.concatenate([orc.rhs(g.uniform_array(p.nvec)) for _ in range(nrhs)])
+        rhs.append(bb)
+        handles.append(G.Gadi.from_problem(p))
+        bs.append(dev64(bb))
+        xs.append(torch.zeros(nrhs * p.nvec, dtype=torch.float64, device="cuda"))
+        alphas.append(a)
+    tol_in = 1e-2 if prec == BF16 else 1e-3
+    st, stats = G.solve_batched(handles, nrhs, bs, xs, alphas, 1.0, prec, 1e-11, 3000,
+                                tol_h=tol_in, tol_s=tol_in, batch_group=2, u_r=G.FP64X2)
+    assert st == G.OK, G.status_str(st)
+    for s, (p, a) in enumerate(systems):
+        orc = O.Oracle(p)
+        for j in range(nrhs):
+            b = rhs[s][j * p.nvec:(j + 1) * p.nvec]
+            xg = xs[s].cpu().numpy()[j * p.nvec:(j + 1) * p.nvec]
+            _, rh, rl, _, _ = orc.residual_dd(FP64, b, xg)
+            assert np.linalg.norm(rh) / np.linalg.norm(b) <= 1e-11
+            x1 = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+            st1, s1 = handles[s].solve(dev64(b), x1, a, 1.0, prec, 1e-11, 3000, tol_h=tol_in, tol_s=tol_in,
+                                       u_r=G.FP64X2)
+            assert st1 == G.OK
+            u = stats[s * nrhs + j]
+            assert abs(u["outer_its"] - s1["outer_its"]) <= max(2, BAND[prec] * s1["outer_its"])
+    for h in handles:
+        h.close()
