@@ -31,6 +31,10 @@ CASES = {
     # shared memory (4-5 rows per block, and 1-2 rows per block)
     "2d_tall": lambda: conv_diff_2d(64, 112, ny=700),
     "2d_slab1": lambda: conv_diff_2d(40, 113, ny=170),
+    # resident H-solve with fewer 16-byte chunks per row than threads (the
+    # block's rows split into parts) and with more (two column passes)
+    "2d_narrow_tall": lambda: conv_diff_2d(8, 116, ny=400),
+    "2d_wide_tall": lambda: conv_diff_2d(2560, 117, ny=200),
     "3d_vec": lambda: conv_diff_3d(16, 106),
     "3d_ragged": lambda: (Problem(K_3D7, 7, 5, 9, 1.0 / 8, (13.0, 29.0, 41.0)),
                           SplitMix64(111).uniform_array(7 * 5 * 9)),
