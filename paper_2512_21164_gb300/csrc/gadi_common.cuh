@@ -267,6 +267,13 @@ __device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long
     return old;
 }
 
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long *p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 struct GridSync {
     unsigned long long *counter; // zeroed before launch
     int *abort_flag;             // zeroed before launch; 1 = a wait timed out
@@ -303,6 +310,44 @@ struct GridSync {
                     }
                     __nanosleep(32);
                 }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+
+    // sync() in two halves.  arrive() publishes the block's writes (release
+    // add; thread 0's value is the count after its add); wait(arrived)
+    // returns once every block has arrived.  Between them the block may
+    // only read data no other block wrote since the previous barrier.
+    __device__ unsigned long long arrive() const
+    {
+        __syncthreads();
+        unsigned long long arrived = 0ull;
+        if (threadIdx.x == 0) arrived = atom_add_release_u64(counter, 1ull) + 1ull;
+        return arrived;
+    }
+    __device__ bool wait(unsigned long long arrived) const
+    {
+        __shared__ int s_ok;
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            const unsigned long long target =
+                (arrived >> 32) == 0ull
+                    ? (unsigned long long)((((unsigned)arrived + nblocks - 1u) / nblocks) * nblocks)
+                    : ((arrived + nblocks - 1ull) / nblocks) * nblocks;
+            // at least one acquire load, also when this block arrived last
+            const unsigned long long t0 = globaltimer_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u64(counter) < target) {
+                if (ld_volatile_int(abort_flag)) { ok = 0; break; }
+                if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+                    atomicExch(abort_flag, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
             s_ok = ok;
         }

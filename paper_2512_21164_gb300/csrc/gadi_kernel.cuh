@@ -1119,6 +1119,14 @@ struct StencilImpl {
     // global loads of the resident phases have no dependency chain, so U of
     // them are kept in flight per thread instead of one per row
     static constexpr int RES_U = PREC == P_BF16 ? 2 : 4;
+    // rows of z and r the H2 march keeps in flight ahead of the one it updates
+    static constexpr int RES_PD = PREC == P_BF16 ? 3 : 4;
+    // the first RES_PD rows of z and r of a thread's first column pass: the
+    // H2 march starts from them, and they can be loaded while the barrier
+    // of the p.(Hp) sum is still open (they are this block's own rows)
+    struct ResRing {
+        S z[RES_PD][WI], r[RES_PD][WI];
+    };
     // p = fl_s(r + beta p_old) on the slab and its halo rows, then the sum of
     // p.(H p) over the slab
     __device__ GADI_RES_FN void h1_res(int j, C beta, AT (&acc)[2]) const
@@ -1176,19 +1184,31 @@ struct StencilImpl {
             }
             __syncthreads();
             AT a = AT(0);
-            res_march<false>(false, C(0), a);
+            ResRing none;
+            res_march<false>(false, C(0), a, none, false);
             acc[0] = a;
             acc[1] = AT(0);
         } else {
             acc[0] = acc[1] = AT(0);
         }
     }
-    // z = fl_s(z + a p), r = fl_s(r - a H p) on the slab, p from shared memory
-    __device__ GADI_RES_FN void h2_res(bool first, C a_, AT (&acc)[2]) const
+    // load the ring the H2 march starts from (see ResRing)
+    __device__ GADI_RES_FN void h2_res_pre(bool first, ResRing &q) const
+    {
+        if constexpr (RES_OK) {
+            int ya, yb;
+            res_rows(ya, yb);
+            const ResMap m = res_map(yb - ya, ne / WI);
+            res_ring_load(first, m, ya, m.cx0, q);
+        }
+    }
+    // z = fl_s(z + a p), r = fl_s(r - a H p) on the slab, p from shared
+    // memory; q: the ring of the first column pass, already loaded
+    __device__ GADI_RES_FN void h2_res(bool first, C a_, AT (&acc)[2], ResRing &q) const
     {
         if constexpr (RES_OK) {
             AT s = AT(0);
-            res_march<true>(first, a_, s);
+            res_march<true>(first, a_, s, q, true);
             acc[0] = s;
             acc[1] = AT(0);
         } else {
@@ -1234,10 +1254,24 @@ struct StencilImpl {
     // or part edge).  UPD = false: acc += p.(H p).  UPD = true: the H2
     // update of z and r, whose rows are prefetched PD steps ahead, and
     // acc += r.r.
-    template <bool UPD>
-    __device__ void res_march(bool first, C a_, AT &acc) const
+    __device__ void res_ring_load(bool first, const ResMap &m, int ya, int cx, ResRing &q) const
     {
-        constexpr int W = WI, PD = PREC == P_BF16 ? 3 : 4;
+        if (!m.act || cx >= ne / WI) return;
+        const size_t o = (size_t)(ya + m.r0) * ne + (size_t)cx * WI;
+        const S *zp = (const S *)P.z + o, *rp = (const S *)P.r + o;
+#pragma unroll
+        for (int k = 0; k < RES_PD; k++) {
+            if (m.r0 + k < m.r1) {
+                if (!first) VecIO<S, WI>::load(zp + (size_t)k * ne, q.z[k]);
+                VecIO<S, WI>::load(rp + (size_t)k * ne, q.r[k]);
+            }
+        }
+    }
+    // pre: the ring of column pass 0 is already in q (UPD only)
+    template <bool UPD>
+    __device__ void res_march(bool first, C a_, AT &acc, ResRing &q, bool pre) const
+    {
+        constexpr int W = WI, PD = RES_PD;
         using A2 = typename InnerAr<PREC>::T;
         int ya, yb;
         res_rows(ya, yb);
@@ -1257,15 +1291,10 @@ struct StencilImpl {
             const float *up_p = sp + (size_t)(m.r0 + 2) * ne + x0;
             S *zp = (S *)P.z + ((size_t)(ya + m.r0) * ne + x0);
             S *rp = (S *)P.r + ((size_t)(ya + m.r0) * ne + x0);
-            S zq[PD][W], rq[PD][W];
+            S (&zq)[PD][W] = q.z;
+            S (&rq)[PD][W] = q.r;
             if constexpr (UPD) {
-#pragma unroll
-                for (int k = 0; k < PD; k++) {
-                    if (col && m.r0 + k < m.r1) {
-                        if (!first) VecIO<S, W>::load(zp + (size_t)k * ne, zq[k]);
-                        VecIO<S, W>::load(rp + (size_t)k * ne, rq[k]);
-                    }
-                }
+                if (!(pre && cp == 0)) res_ring_load(first, m, ya, cx, q);
             }
             float dn[W], c[W], up[W];
 #pragma unroll

@@ -219,8 +219,10 @@ struct CsrImpl {
     }
     __device__ void s_pointwise(C) const {}
     // (the SM-resident H-solve exists for the 2D stencil class only)
+    struct ResRing {};
     __device__ void h1r(int, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
-    __device__ void h2r(bool, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
+    __device__ void h2pre(bool, ResRing &) const {}
+    __device__ void h2r(bool, C, AT (&acc)[2], ResRing &) const { acc[0] = acc[1] = AT(0); }
 };
 
 // Adapter giving the stencil implementation the same (bool-returning,
@@ -286,8 +288,10 @@ struct StencilAdapter {
         return true;
     }
     __device__ void s_pointwise(C gamma) const { si.s_pointwise(gamma); }
+    using ResRing = typename SI::ResRing;
     __device__ void h1r(int j, C beta, AT (&acc)[2]) const { si.h1_res(j, beta, acc); }
-    __device__ void h2r(bool first, C a, AT (&acc)[2]) const { si.h2_res(first, a, acc); }
+    __device__ void h2pre(bool first, ResRing &q) const { si.h2_res_pre(first, q); }
+    __device__ void h2r(bool first, C a, AT (&acc)[2], ResRing &q) const { si.h2_res(first, a, acc, q); }
 };
 
 // ---------------------------------------------------------------------------
@@ -331,6 +335,24 @@ struct Runner {
         slot ^= 1;
         return true;
     }
+    // reduce() in two halves: between them the block may do work that reads
+    // nothing other blocks wrote since the previous barrier
+    template <class RT>
+    __device__ unsigned long long reduce_begin(const RT (&acc)[2])
+    {
+        const int G = I.vg.n;
+        RT *part = reinterpret_cast<RT *>(P.part + (size_t)slot * 2 * G);
+        block_partials_write<2, RT>(acc, part, G, I.vg.b);
+        return gs.arrive();
+    }
+    template <class RT>
+    __device__ bool reduce_end(unsigned long long arrived, RT (&out)[2])
+    {
+        if (!gs.wait(arrived)) return false;
+        grid_partials_sum<2, RT>(reinterpret_cast<const RT *>(P.part + (size_t)slot * 2 * I.vg.n), I.vg.n, out);
+        slot ^= 1;
+        return true;
+    }
 
     // CG on H = alpha I + M (right-hand side already in P.r, ||rhs||^2 = rr0).
     // Returns iterations, or -1 if a barrier gave up.
@@ -352,15 +374,17 @@ struct Runner {
             // the resident instantiation runs only with P.resident set
             if constexpr (Impl::RESIDENT) {
                 I.h1r(j, beta, acc);
-            } else if (!I.h1(j == 0, beta, pold, pnew, acc, gs)) {
-                return -1;
-            }
-            if (!reduce(acc, sum)) return -1;
-            const C a = A::div(rr, (C)sum[0]);
-            if constexpr (Impl::RESIDENT) {
-                I.h2r(j == 0, a, acc);
-            } else if (!I.h2(j == 0, a, pnew, acc, gs)) {
-                return -1;
+                // the first rows of z and r the update needs are loaded
+                // while the barrier of p.(Hp) is open
+                const unsigned long long arrived = reduce_begin(acc);
+                typename Impl::ResRing ring;
+                I.h2pre(j == 0, ring);
+                if (!reduce_end(arrived, sum)) return -1;
+                I.h2r(j == 0, A::div(rr, (C)sum[0]), acc, ring);
+            } else {
+                if (!I.h1(j == 0, beta, pold, pnew, acc, gs)) return -1;
+                if (!reduce(acc, sum)) return -1;
+                if (!I.h2(j == 0, A::div(rr, (C)sum[0]), pnew, acc, gs)) return -1;
             }
             if (!reduce(acc, sum)) return -1;
             const C rn = (C)sum[0];
