@@ -122,8 +122,9 @@ typedef struct {
 /* Solver options.  Defaults (gadi_opts_default): tol_h = tol_s = 1e-3 (1e-2
  * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
- * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 1,
- * u_r = GADI_FP64. */
+ * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 2
+ * (1 for BF16, where tensor memory measured slower), u_r = GADI_FP64.  The
+ * step entry gadi_step_solve_h takes the same h_resident default. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
     double tol_s;          /* inner CGNR tolerance on S (normal residual)   */
@@ -144,10 +145,16 @@ typedef struct {
     int h_resident;        /* 2D real class, FP32/BF16, 16-byte aligned rows:
                               1 = CG on H keeps its search direction p in
                               shared memory when a block's rows (+2 halo
-                              rows) fit without lowering occupancy; 0 =
-                              always stream p through global memory.  Same
-                              arithmetic either way; only the order of the
-                              grid-wide sums differs.                       */
+                              rows) fit without lowering occupancy; 2 = as
+                              1, and z and r of the block's rows also stay
+                              on chip, in tensor memory (TMEM), when each
+                              thread's share fits 16 slots of 16 bytes
+                              (e.g. 2048 x 2048, FP32 or BF16, on 152
+                              SMs), else as 1; 0 = always
+                              stream p through global memory.  Same
+                              arithmetic in all three; 1 and 2 give the
+                              same bits, 0 differs in the order of the
+                              grid-wide sums.  Other values: INVALID.       */
     gadi_prec u_r;         /* residual precision u_r (Sec. 3.1, u_r <= u):
                               GADI_FP64 or GADI_FP64X2; every problem
                               class, single and batched solves             */
@@ -164,7 +171,9 @@ typedef struct {
     int blocks;             /* persistent blocks launched                    */
     double alpha;           /* alpha of the last run (after any restarts)    */
     int restarts;           /* alpha restarts taken (Sec. 4.3 step 3)        */
-    int h_resident;         /* 1 if the H-solve kept p in shared memory      */
+    int h_resident;         /* the H-solve taken: 0 streaming, 1 p in shared
+                               memory, 2 p in shared and z, r in tensor
+                               memory                                        */
 } gadi_stats;
 
 typedef struct gadi_handle gadi_handle;

@@ -280,6 +280,29 @@ bool params_aligned(const Params &P)
     return true;
 }
 
+// TMEM slots per thread of the tensor-memory H-solve: 512 columns shared by
+// the kThreads / 128 warps of a lane quarter, 8 columns (z and r) a slot
+constexpr int kTmSlots = 512 / (kThreadsHost / 128) / 8;
+
+// slots the tensor-memory H-solve needs per thread: the column passes times
+// the march steps of the block with the most rows (the device's res_map)
+long long tm_slots(long long nxw, long long ny, long long blocks)
+{
+    long long worst = 0;
+    for (long long b = 0; b < blocks; ++b) {
+        const long long R = (b + 1) * ny / blocks - b * ny / blocks;
+        long long need;
+        if (nxw >= kThreadsHost) {
+            need = ((nxw + kThreadsHost - 1) / kThreadsHost) * R;
+        } else {
+            const long long np = kThreadsHost / nxw;
+            need = (R + np - 1) / np;
+        }
+        worst = std::max(worst, need);
+    }
+    return worst;
+}
+
 const void *pick_kernel(gadi_handle *h, int prec, bool aligned, size_t *smem, int *vec_out = nullptr, int dd = 0)
 {
     *smem = 0;
@@ -327,7 +350,11 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     // plus one halo row on each side in shared memory (floats); taken only
     // where every block owns at least one row and the extra shared memory
     // keeps the blocks this launch needs co-resident on each SM
+    // With h_resident = 2, z and r of the H-solve also stay on chip, in
+    // tensor memory, when every thread's march chunks fit its 16 slots
+    // (tm_slots); the TMEM kernel then runs alone on each SM.
     if (P.resident) {
+        const int want = P.resident;
         P.resident = 0;
         if (h->kind == GADI_STENCIL_2D5 && prec != P_FP64 && vec && blocks <= h->ny &&
             (P.mode == MODE_SOLVE || P.mode == MODE_SOLVE_H)) {
@@ -336,13 +363,16 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
             int optin = 0;
             CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
             const size_t rsz = std::max(rs, smem);
-            const void *kr = kernel_2d5_res(prec, P.ur_dd);
-            if (kr && rsz <= (size_t)optin) {
+            const int elems16 = prec == P_FP32 ? 4 : 8;
+            const bool tm = want == 2 && blocks <= h->nsm && tm_slots(h->nx / elems16, h->ny, blocks) <= kTmSlots;
+            for (int variant = tm ? 2 : 1; variant >= 1 && !P.resident; --variant) {
+                const void *kr = variant == 2 ? kernel_2d5_tm(prec, P.ur_dd) : kernel_2d5_res(prec, P.ur_dd);
+                if (!kr || rsz > (size_t)optin) continue;
                 CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
                 int per_sm_r = 0;
                 CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, kr, kThreadsHost, rsz));
-                if ((long long)per_sm_r * h->nsm >= blocks) {
-                    P.resident = 1;
+                if ((long long)per_sm_r * h->nsm >= blocks && (variant == 1 || per_sm_r == 1)) {
+                    P.resident = variant;
                     smem = rsz;
                     k = kr;
                 }
@@ -550,7 +580,7 @@ gadi_status opts_check(const gadi_opts &o)
 {
     if (!(o.tol_h >= 0) || !(o.tol_s >= 0) || o.maxit_inner < 0 || o.inner_stag < 0 || o.outer_stag_window < 0)
         return GADI_ERR_INVALID;
-    if (o.h_resident != 0 && o.h_resident != 1) return GADI_ERR_INVALID;
+    if (o.h_resident < 0 || o.h_resident > 2) return GADI_ERR_INVALID;
     if (o.u_r != GADI_FP64 && o.u_r != GADI_FP64X2) return GADI_ERR_INVALID;
     return GADI_OK;
 }
@@ -576,7 +606,9 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->hist = nullptr;
     o->batch_group = 0;
     o->alpha_restarts = 0;
-    o->h_resident = 1;
+    // tensor-memory z and r measured faster for FP32 (CG on H at 2048^2:
+    // 12.0 vs 13.2 us per iteration) and slower for BF16 (17.6 vs 16.3)
+    o->h_resident = (u_low == GADI_BF16) ? 1 : 2;
     o->u_r = GADI_FP64;
 }
 
@@ -1250,7 +1282,7 @@ gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, con
     P.maxit_inner = maxit;
     P.inner_stag = stag;
     P.maxit = 1;
-    P.resident = 1;
+    P.resident = prec == P_BF16 ? 1 : 2; // as gadi_opts_default
     if ((s = launch(h, prec, P, 0, st, nullptr)) != GADI_OK) return s;
     if ((s = finish(h, st)) != GADI_OK) return s;
     if (its) *its = (int)h->h_ctl->inner_h;

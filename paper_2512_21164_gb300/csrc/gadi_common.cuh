@@ -357,6 +357,65 @@ struct GridSync {
 };
 
 // ---------------------------------------------------------------------------
+// tensor memory (TMEM) as per-thread storage
+// ---------------------------------------------------------------------------
+// TMEM is the 128-lane x 512-column (32-bit) on-chip memory of a Blackwell SM
+// that tcgen05 tensor-core instructions accumulate into.  The H-solve uses
+// it only as storage: thread i of warp w keeps its values in lane
+// 32 (w % 4) + i (a warp may reach only its lane quarter) and in a column
+// range of its own.  The 32x32b shape moves one 32-bit word per lane and
+// column; x4: four consecutive columns, i.e. 16 bytes per thread.  All of
+// these are warp-collective (.sync.aligned): every lane of the warp executes
+// them with the same address.  Loads complete at tcgen05.wait::ld, stores at
+// tcgen05.wait::st.
+__device__ __forceinline__ void tmem_alloc(unsigned *smem_dst, unsigned ncols)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld4(unsigned taddr, unsigned (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st4(unsigned taddr, const unsigned (&v)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+// wait for this thread's outstanding TMEM loads; the registers they fill
+// pass through the statement so that no use is scheduled before it
+template <int N>
+__device__ __forceinline__ void tmem_wait_ld(unsigned (&v)[N][4])
+{
+    static_assert(N == 2 || N == 4, "tmem_wait_ld: 2 or 4 groups");
+    if constexpr (N == 2) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[1][0]), "+r"(v[1][1]),
+                       "+r"(v[1][2]), "+r"(v[1][3])::"memory");
+    } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[1][0]), "+r"(v[1][1]),
+                       "+r"(v[1][2]), "+r"(v[1][3]), "+r"(v[2][0]), "+r"(v[2][1]), "+r"(v[2][2]), "+r"(v[2][3]),
+                       "+r"(v[3][0]), "+r"(v[3][1]), "+r"(v[3][2]), "+r"(v[3][3])::"memory");
+    }
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // deterministic reductions
 // ---------------------------------------------------------------------------
 // Each block reduces NV per-thread partial sums (type RT) in a fixed tree and

@@ -8,11 +8,14 @@ namespace gadi {
 const void *kernel_2d5(int prec, int vec, int dd = 0);
 // the 2D kernel with the SM-resident H-solve (FP32/BF16, 16-byte path; else null)
 const void *kernel_2d5_res(int prec, int dd = 0);
+// the same with z and r of the H-solve in tensor memory
+const void *kernel_2d5_tm(int prec, int dd = 0);
 const void *kernel_3d7(int prec, int vec, int dd = 0);
 const void *kernel_c2d5(int prec, int vec, int dd = 0);
 const void *kernel_csr(int prec, int dd = 0);
 const void *kernel_2d5_dd(int prec, int vec);
 const void *kernel_2d5_res_dd(int prec);
+const void *kernel_2d5_tm_dd(int prec);
 const void *kernel_3d7_dd(int prec, int vec);
 const void *kernel_c2d5_dd(int prec, int vec);
 // dynamic shared memory (bytes) the selected stencil kernel needs at launch

@@ -8,14 +8,14 @@ const void *kernel_2d5_dd(int prec, int vec)
 {
     switch (prec) {
     case P_FP64:
-        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 2, 2, false, true>
-                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 1, 1, false, true>;
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 2, 2, 0, true>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP64, 1, 1, 0, true>;
     case P_FP32:
-        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, false, true>
-                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 1, 1, false, true>;
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, 0, true>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 1, 1, 0, true>;
     case P_BF16:
-        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, false, true>
-                   : (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 1, 1, false, true>;
+        return vec ? (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, 0, true>
+                   : (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 1, 1, 0, true>;
     }
     return nullptr;
 }
@@ -23,9 +23,9 @@ const void *kernel_2d5_res_dd(int prec)
 {
     switch (prec) {
     case P_FP32:
-        return (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, true, true>;
+        return (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, 1, true>;
     case P_BF16:
-        return (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, true, true>;
+        return (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, 1, true>;
     }
     return nullptr;
 }

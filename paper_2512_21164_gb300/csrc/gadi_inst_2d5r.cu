@@ -9,9 +9,9 @@ const void *kernel_2d5_res(int prec, int dd)
     if (dd) return kernel_2d5_res_dd(prec);
     switch (prec) {
     case P_FP32:
-        return (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, true>;
+        return (const void *)gadi_stencil_kernel<K_2D5, P_FP32, 4, 2, 1>;
     case P_BF16:
-        return (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, true>;
+        return (const void *)gadi_stencil_kernel<K_2D5, P_BF16, 8, 2, 1>;
     }
     return nullptr;
 }

@@ -1364,6 +1364,274 @@ struct StencilImpl {
         }
     }
 
+    // ---- z and r in tensor memory ----
+    // The TMEM variant of the resident H-solve also keeps z and r of the
+    // block's own rows on chip for the whole CG solve: each thread stores
+    // its march chunks (column pass cp, step s -> slot cp * rmax + s) in
+    // TMEM, z in the slot's first four columns and r in the next four (16
+    // bytes each).  Global memory then sees only what other blocks need: r
+    // of the slab's first and last row (the neighbours' halo) every
+    // iteration, and z once, when the solve ends.  Same arithmetic as the
+    // L2 variant, so both give the same bits.
+    static constexpr int TM_COLS = 512 / (kThreads / 128); // TMEM columns per warp
+    static constexpr int TM_SLOTS = TM_COLS / 8;            // chunks of z and r per thread
+    static constexpr bool TM_OK = RES_OK && (kThreads % 128) == 0 && TM_SLOTS >= 1;
+    unsigned tm = 0; // TMEM base address of the block's allocation (512 columns)
+    __device__ unsigned tm_addr(int slot, int which) const
+    {
+        const int w = threadIdx.x >> 5;
+        return tm + ((unsigned)((w & 3) * 32) << 16) + (unsigned)((w >> 2) * TM_COLS + slot * 8 + which * 4);
+    }
+    // true if every thread's chunks fit its TMEM columns (the host checks the
+    // same before it picks this variant)
+    __device__ bool tm_fits() const
+    {
+        int ya, yb;
+        res_rows(ya, yb);
+        const ResMap m = res_map(yb - ya, ne / WI);
+        return m.ncp * m.rmax <= TM_SLOTS;
+    }
+    template <int W>
+    __device__ static void to_words(const S (&v)[W], unsigned (&w)[4])
+    {
+        static_assert(W * sizeof(S) == 16, "16-byte chunks");
+        memcpy(w, v, 16);
+    }
+    template <int W>
+    __device__ static void from_words(const unsigned (&w)[4], S (&v)[W])
+    {
+        memcpy(v, w, 16);
+    }
+    // p = fl_s(r + beta p) (p = r at j = 0) for one 16-byte chunk of p in
+    // shared memory, as in h1_res
+    template <int W>
+    __device__ static void p_chunk(bool first, C beta, const S (&rv)[W], float *pp)
+    {
+        using A2 = typename InnerAr<PREC>::T;
+        float4 *d4 = reinterpret_cast<float4 *>(pp);
+#pragma unroll
+        for (int v = 0; v < W; v += 4) {
+            float4 t;
+            if (first) {
+                t = make_float4(PT::ld(rv[v]), PT::ld(rv[v + 1]), PT::ld(rv[v + 2]), PT::ld(rv[v + 3]));
+            } else {
+                t = d4[v / 4];
+                t.x = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[v]))));
+                t.y = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[v + 1]))));
+                t.z = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[v + 2]))));
+                t.w = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[v + 3]))));
+            }
+            d4[v / 4] = t;
+        }
+    }
+    // p update and p.(H p), r of the own rows from TMEM (at j = 0 from
+    // global memory, then kept), the halo rows from the neighbours' r
+    __device__ GADI_RES_FN void h1_tm(int j, C beta, AT (&acc)[2]) const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI, U = 4;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            float *sp = res_smem();
+            const S *r = (const S *)P.r;
+            const bool first = j == 0;
+            if (first) {
+                if (ya == 0)
+                    for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[i] = 0.f;
+                if (yb == ny)
+                    for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[(size_t)(R + 1) * ne + i] = 0.f;
+            }
+            // halo rows ya - 1 and yb (smem rows 0 and R + 1)
+            for (int i = threadIdx.x; i < 2 * nxw; i += blockDim.x) {
+                const bool lo = i < nxw;
+                if (lo ? ya == 0 : yb == ny) continue;
+                const int c = lo ? i : i - nxw, row = lo ? -1 : R;
+                S rv[W];
+                VecIO<S, W>::load(r + ((long long)(ya + row) * ne + (long long)c * W), rv);
+                p_chunk<W>(first, beta, rv, sp + (size_t)(row + 1) * ne + (size_t)c * W);
+            }
+            // own rows, in the march's thread map
+            const ResMap m = res_map(R, nxw);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const int sb = cp * m.rmax;
+                for (int s0 = 0; s0 < m.rmax; s0 += U) {
+                    unsigned w[U][4];
+#pragma unroll
+                    for (int u = 0; u < U; u++) w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
+                    if (first) {
+                        S rv[U][W];
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            if (col && m.r0 + s0 + u < m.r1)
+                                VecIO<S, W>::load(r + ((size_t)(ya + m.r0 + s0 + u) * ne + x0), rv[u]);
+                            else
+                                for (int v = 0; v < W; v++) rv[u][v] = PT::st(C(0));
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; u++) {
+                            to_words<W>(rv[u], w[u]);
+                            if (s0 + u < m.rmax) tmem_st4(tm_addr(sb + s0 + u, 1), w[u]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, 1), w[u]);
+                        tmem_wait_ld<U>(w);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        if (col && m.r0 + s0 + u < m.r1) {
+                            S rv[W];
+                            from_words<W>(w[u], rv);
+                            p_chunk<W>(first, beta, rv, sp + (size_t)(m.r0 + s0 + u + 1) * ne + x0);
+                        }
+                    }
+                }
+            }
+            if (first) tmem_wait_st();
+            __syncthreads();
+            AT a = AT(0);
+            ResRing none;
+            res_march<false>(false, C(0), a, none, false);
+            acc[0] = a;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    // z = fl_s(z + a p), r = fl_s(r - a H p) with z and r in TMEM; r of the
+    // slab's first and last row also to global memory (the neighbours' halo)
+    __device__ GADI_RES_FN void h2_tm(bool first, C a_, AT (&acc)[2]) const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI;
+            using A2 = typename InnerAr<PREC>::T;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            const float *sp = res_smem();
+            const ResMap m = res_map(R, nxw);
+            const int lane = threadIdx.x & 31;
+            AT s2 = AT(0);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const bool lsh = lane > 0 && cx > 0, rsh = lane < 31 && cx + 1 < nxw;
+                const bool xlo = x0 > 0, xhi = x0 + W < ne;
+                const float *up_p = sp + (size_t)(m.r0 + 2) * ne + x0;
+                S *rg = (S *)P.r + ((size_t)(ya + m.r0) * ne + x0);
+                const int sb = cp * m.rmax;
+                unsigned w[2][4]; // z, r of the current step
+#pragma unroll
+                for (int k = 0; k < 2; k++) w[k][0] = w[k][1] = w[k][2] = w[k][3] = 0u;
+                if (!first) tmem_ld4(tm_addr(sb, 0), w[0]);
+                tmem_ld4(tm_addr(sb, 1), w[1]);
+                float dn[W], c[W], up[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) dn[v] = c[v] = up[v] = 0.f;
+                if (col) {
+                    res_row<W>(up_p - 2 * (size_t)ne, dn);
+                    res_row<W>(up_p - (size_t)ne, c);
+                }
+                int left = col ? m.r1 - m.r0 : 0;
+                for (int st = 0; st < m.rmax; ++st) {
+                    const bool ok = left > 0;
+                    if (ok) res_row<W>(up_p, up);
+                    float cl = __shfl_up_sync(0xffffffffu, c[W - 1], 1);
+                    float cr = __shfl_down_sync(0xffffffffu, c[0], 1);
+                    C q[W];
+#pragma unroll
+                    for (int v = 0; v < W; v++) q[v] = C(0);
+                    if (ok) {
+                        if (!lsh) cl = xlo ? up_p[-(ptrdiff_t)ne - 1] : 0.f;
+                        if (!rsh) cr = xhi ? up_p[-(ptrdiff_t)ne + W] : 0.f;
+#pragma unroll
+                        for (int v = 0; v < W; v++) {
+                            const float wv = v > 0 ? c[v - 1] : cl, ev = v + 1 < W ? c[v + 1] : cr;
+                            q[v] = stencil_at<A2, C, false, false>(ch.d, ch.c, C(0), c[v], wv, ev, dn[v], up[v], C(0),
+                                                                  C(0), C(0), false);
+                        }
+                    }
+                    tmem_wait_ld<2>(w);
+                    S zv[W], rv[W];
+                    from_words<W>(w[0], zv);
+                    from_words<W>(w[1], rv);
+                    if (ok) {
+#pragma unroll
+                        for (int v = 0; v < W; v++) {
+                            zv[v] = PT::st(first ? A2::mul(a_, c[v]) : A2::madd(a_, c[v], PT::ld(zv[v])));
+                            rv[v] = PT::st(A2::madd(-a_, q[v], PT::ld(rv[v])));
+                            const C t = PT::ld(rv[v]);
+                            s2 += (AT)t * (AT)t;
+                        }
+                        const int row = m.r0 + st;
+                        if ((row == 0 && ya > 0) || (row == R - 1 && yb < ny)) VecIO<S, W>::store(rg, rv);
+                    }
+                    to_words<W>(zv, w[0]);
+                    to_words<W>(rv, w[1]);
+                    tmem_st4(tm_addr(sb + st, 0), w[0]);
+                    tmem_st4(tm_addr(sb + st, 1), w[1]);
+                    if (st + 1 < m.rmax) {
+                        if (!first) tmem_ld4(tm_addr(sb + st + 1, 0), w[0]);
+                        tmem_ld4(tm_addr(sb + st + 1, 1), w[1]);
+                    }
+                    --left;
+                    up_p += ne;
+                    rg += ne;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        dn[v] = c[v];
+                        c[v] = up[v];
+                    }
+                }
+            }
+            tmem_wait_st();
+            acc[0] = s2;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    // z of the own rows from TMEM to global memory (end of the H-solve)
+    __device__ void h_flush_tm() const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI, U = 4;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int nxw = ne / W;
+            const ResMap m = res_map(yb - ya, nxw);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const int sb = cp * m.rmax;
+                for (int s0 = 0; s0 < m.rmax; s0 += U) {
+                    unsigned w[U][4];
+#pragma unroll
+                    for (int u = 0; u < U; u++) w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, 0), w[u]);
+                    tmem_wait_ld<U>(w);
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        if (col && m.r0 + s0 + u < m.r1) {
+                            S zv[W];
+                            from_words<W>(w[u], zv);
+                            VecIO<S, W>::store((S *)P.z + ((size_t)(ya + m.r0 + s0 + u) * ne + x0), zv);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
     // complex class: S = alpha I + i T (T = sigma I or diag(T_i)),
     // y = fl_s(g / (alpha + i T_i)) pointwise
     __device__ void s_pointwise(C gamma) const

@@ -220,14 +220,18 @@ struct CsrImpl {
     __device__ void s_pointwise(C) const {}
     // (the SM-resident H-solve exists for the 2D stencil class only)
     struct ResRing {};
+    static constexpr bool TMEM = false;
+    __device__ void hflush() const {}
     __device__ void h1r(int, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
     __device__ void h2pre(bool, ResRing &) const {}
     __device__ void h2r(bool, C, AT (&acc)[2], ResRing &) const { acc[0] = acc[1] = AT(0); }
 };
 
 // Adapter giving the stencil implementation the same (bool-returning,
-// barrier-taking) interface as the CSR one.
-template <class SI, bool RES = false>
+// barrier-taking) interface as the CSR one.  RES: 0 streaming H-solve,
+// 1 SM-resident p (z and r in global memory / L2), 2 SM-resident p with z
+// and r in tensor memory.
+template <class SI, int RES = 0>
 struct StencilAdapter {
     using S = typename SI::S;
     using C = typename SI::C;
@@ -235,7 +239,8 @@ struct StencilAdapter {
     using AT = typename SI::AT;
     static constexpr int K = SI::K;
     // the SM-resident H-solve is compiled in where it exists and RES allows
-    static constexpr bool RESIDENT = SI::RES_OK && RES;
+    static constexpr bool RESIDENT = SI::RES_OK && RES >= 1;
+    static constexpr bool TMEM = SI::TM_OK && RES == 2;
     SI si;
     VGrid vg;
     __device__ StencilAdapter(const Params &p, VGrid g) : si(p, g), vg(g) {}
@@ -289,9 +294,25 @@ struct StencilAdapter {
     }
     __device__ void s_pointwise(C gamma) const { si.s_pointwise(gamma); }
     using ResRing = typename SI::ResRing;
-    __device__ void h1r(int j, C beta, AT (&acc)[2]) const { si.h1_res(j, beta, acc); }
-    __device__ void h2pre(bool first, ResRing &q) const { si.h2_res_pre(first, q); }
-    __device__ void h2r(bool first, C a, AT (&acc)[2], ResRing &q) const { si.h2_res(first, a, acc, q); }
+    __device__ void h1r(int j, C beta, AT (&acc)[2]) const
+    {
+        if constexpr (TMEM)
+            si.h1_tm(j, beta, acc);
+        else
+            si.h1_res(j, beta, acc);
+    }
+    __device__ void h2pre(bool first, ResRing &q) const
+    {
+        if constexpr (!TMEM) si.h2_res_pre(first, q);
+    }
+    __device__ void h2r(bool first, C a, AT (&acc)[2], ResRing &q) const
+    {
+        if constexpr (TMEM)
+            si.h2_tm(first, a, acc);
+        else
+            si.h2_res(first, a, acc, q);
+    }
+    __device__ void hflush() const { si.h_flush_tm(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -399,6 +420,13 @@ struct Runner {
             }
             beta = A::div(rn, rr);
             rr = rn;
+        }
+        if constexpr (Impl::TMEM) {
+            // z leaves tensor memory; the S-solve reads it across blocks
+            if (its > 0) {
+                I.hflush();
+                if (!gs.sync()) return -1;
+            }
         }
         return its;
     }
@@ -527,16 +555,43 @@ struct Runner {
     }
 };
 
-// RES = true: the instantiation with the SM-resident H-solve (2D real class,
+// RES = 1: the instantiation with the SM-resident H-solve (2D real class,
 // FP32/BF16, 16-byte path), a kernel of its own so that its register needs
-// leave the streaming kernels' code alone
-template <int KIND, int PREC, int WI, int WR, bool RES = false, bool DD = false>
+// leave the streaming kernels' code alone; RES = 2: the same with z and r
+// of the H-solve in tensor memory.  The RES = 2 kernel allocates all 512
+// TMEM columns of its SM for the launch (it runs one block per SM: its
+// register file use leaves room for no other block) and frees them on
+// every way out.
+template <int KIND, int PREC, int WI, int WR, int RES = 0, bool DD = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
     using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR, DD>, RES>;
     Ad I(P, whole_grid());
-    Runner<PREC, Ad> R(P, I);
-    R.run();
+    if constexpr (Ad::TMEM) {
+        __shared__ unsigned s_tm;
+        const bool w0 = threadIdx.x < 32;
+        if (w0) {
+            tmem_alloc(&s_tm, 512u);
+            tmem_relinquish();
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        I.si.tm = s_tm;
+        if (I.si.tm_fits()) {
+            Runner<PREC, Ad> R(P, I);
+            R.run();
+        } else if (threadIdx.x == 0) {
+            atomicExch(P.abort_flag, 1); // the host refuses such shapes first
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        if (w0) tmem_dealloc(s_tm, 512u);
+    } else {
+        Runner<PREC, Ad> R(P, I);
+        R.run();
+    }
 }
 
 template <int PREC, bool DD = false>

@@ -211,8 +211,8 @@ def test_resident_h_solve_matches_streaming_and_oracle(prec, max_blocks):
     alpha = 2 * alpha_star(p)
     th, ts = _tols(prec)
     xo, so = orc.gadi(b, alpha, 1.0, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts)
-    res = {}
-    for hr in (1, 0):
+    res, xs = {}, {}
+    for hr in (2, 1, 0):
         st, sg, xg, hg = _gpu_solve(p, b, alpha, 1.0, prec, 1e-10, 3000, max_blocks=max_blocks,
                                     h_resident=hr)
         assert st == G.OK, G.status_str(st)
@@ -220,17 +220,62 @@ def test_resident_h_solve_matches_streaming_and_oracle(prec, max_blocks):
         rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
         assert rel <= 1e-10
         assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
-        res[hr] = sg
+        res[hr], xs[hr] = sg, xg
     assert abs(res[1]["outer_its"] - res[0]["outer_its"]) <= max(2, BAND[prec] * res[0]["outer_its"])
     assert abs(res[1]["inner_its_h"] - res[0]["inner_its_h"]) <= 0.1 * res[0]["inner_its_h"] + 2
+    # z and r in tensor memory: the same operations in the same order as 1
+    assert np.array_equal(xs[2], xs[1])
+    for key in ("outer_its", "inner_its_h", "inner_its_s", "relres"):
+        assert res[2][key] == res[1][key]
+
+
+def _tm_slots(nx, ny, prec, blocks, threads=512):
+    """Slots per thread the tensor-memory H-solve needs (16 available)."""
+    nxw = nx // (4 if prec == FP32 else 8)
+    worst = 0
+    for bi in range(blocks):
+        R = (bi + 1) * ny // blocks - bi * ny // blocks
+        need = -(-nxw // threads) * R if nxw >= threads else -(-R // (threads // nxw))
+        worst = max(worst, need)
+    return worst
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("nx,ny,blocks", [(2560, 200, 16), (8, 400, 16), (4096, 160, 16), (2048, 304, 152)])
+def test_tmem_h_solve_same_bits_as_shared_memory_form(prec, nx, ny, blocks):
+    """h_resident = 2 keeps z and r of CG on H in tensor memory when each
+    thread's chunks fit 16 slots, else falls back to 1: either way the result
+    has the same bits as h_resident = 1 (two column passes, row parts of a
+    narrow grid, a shape past the slot limit in FP32)."""
+    import torch
+    p, xt = conv_diff_2d(nx, 212, ny=ny)
+    a0 = alpha_star(p)
+    out = {}
+    with G.Gadi.from_problem(p) as H:
+        xtd = torch.from_numpy(np.ascontiguousarray(xt)).cuda()
+        b = torch.zeros_like(xtd)
+        H.apply(G.OP_A, xtd, b)
+        th, ts = _tols(prec)
+        for hr in (2, 1):
+            x = torch.zeros_like(b)
+            st, s = H.solve(b, x, 4 * a0, 0.0, prec, 1e-12, 4, tol_h=th, tol_s=ts, max_blocks=blocks,
+                            h_resident=hr, check=False)
+            assert st in (G.OK, G.NOT_CONVERGED), G.status_str(st)
+            out[hr] = (s, x.cpu().numpy())
+    want = 2 if _tm_slots(nx, ny, prec, blocks) <= 16 else 1
+    assert out[2][0]["h_resident"] == want and out[1][0]["h_resident"] == 1
+    assert np.array_equal(out[2][1], out[1][1])
+    for key in ("outer_its", "inner_its_h", "inner_its_s", "relres"):
+        assert out[2][0][key] == out[1][0][key]
 
 
 def test_resident_option_validated():
     p, xt = conv_diff_2d(16, 206)
     b = O.Oracle(p).rhs(xt)
     with G.Gadi.from_problem(p) as H:
-        st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, h_resident=2, check=False)
-    assert st == G.ERR_INVALID
+        for bad in (3, -1):
+            st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, h_resident=bad, check=False)
+            assert st == G.ERR_INVALID
 
 
 @pytest.mark.parametrize("name,prec", [("2d", FP32), ("3d", BF16), ("cplx", FP32), ("csr", FP64)])
