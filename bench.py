@@ -39,7 +39,11 @@ TOL_INNER = 1e-3       # default inner tolerance (other configurations)
 TOL_H, TOL_S = 1e-3, 1e-3
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 KERNEL_SOURCES = ["gadi_kernel.cuh", "gadi_solver.cuh", "gadi_common.cuh", "gadi_params.h",
-                  "gadi_inst_2d5.cu", "gadi_inst_2d5r.cu"]
+                  "gadi_inst_2d5.cu", "gadi_inst_2d5r.cu", "gadi_inst_2d5t.cu"]
+
+
+# stats["h_resident"]: the form the CG on H took
+H_SOLVE = {0: "streaming", 1: "p in shared memory", 2: "p in shared memory, z and r in tensor memory"}
 
 
 def kernel_source_hash() -> str:
@@ -94,6 +98,13 @@ class Clocks:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        # wait (3 s at most) for the first sample, taken before the timed
+        # region: nvidia-smi's start-up can hold up the CUDA calls that
+        # launch a step, which the step's events would then count
+        if self.p is not None:
+            import select
+            if select.select([self.p.stdout], [], [], 3.0)[0]:
+                self.p.stdout.readline()
         return self
 
     def __exit__(self, *a):
@@ -259,7 +270,8 @@ def run_ours(args):
         "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(ab), "peak_source": src,
-                     "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve)",
+                     "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve; H-solve: "
+                               + H_SOLVE[mixed_stats["h_resident"]] + ")",
                      "algorithmic_bytes": ab},
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n,
                 "d2h_bytes_per_step": 8 * n},
