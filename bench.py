@@ -271,7 +271,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": measured_traffic(ab), "peak_source": src,
                      "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve; H-solve: "
-                               + H_SOLVE[mixed_stats["h_resident"]] + ")",
+                               + H_SOLVE[mixed_stats["h_resident"]] + "; S-solve: "
+                               + ("p in shared memory, t and y in tensor memory" if mixed_stats.get("s_resident")
+                                  else "streaming") + ")",
                      "algorithmic_bytes": ab},
         "e2e": {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n,
                 "d2h_bytes_per_step": 8 * n},

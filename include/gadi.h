@@ -123,7 +123,8 @@ typedef struct {
  * for BF16), maxit_inner = 1000, inner_stag = 10, outer_stag_window = 50,
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
  * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 2
- * (1 for BF16, where tensor memory measured slower), u_r = GADI_FP64.  The
+ * (1 for BF16, where tensor memory measured slower), u_r = GADI_FP64,
+ * s_resident = 1.  The
  * step entry gadi_step_solve_h takes the same h_resident default. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
@@ -158,6 +159,13 @@ typedef struct {
     gadi_prec u_r;         /* residual precision u_r (Sec. 3.1, u_r <= u):
                               GADI_FP64 or GADI_FP64X2; every problem
                               class, single and batched solves             */
+    int s_resident;        /* with h_resident = 2 taken: 1 = CGNR on S also
+                              keeps its direction p in shared memory (two
+                              halo rows each side) and t, y in tensor
+                              memory when every block owns two rows or
+                              more (S p is recomputed, never stored); 0 =
+                              stream it.  Same arithmetic; the grid-wide
+                              sums' order differs.  Other values: INVALID. */
 } gadi_opts;
 
 typedef struct {
@@ -174,6 +182,9 @@ typedef struct {
     int h_resident;         /* the H-solve taken: 0 streaming, 1 p in shared
                                memory, 2 p in shared and z, r in tensor
                                memory                                        */
+    int s_resident;         /* 1 if CGNR on S also ran resident (h_resident
+                               = 2 and every block owns >= 2 rows): p in
+                               shared memory, t and y in tensor memory       */
 } gadi_stats;
 
 typedef struct gadi_handle gadi_handle;

@@ -353,6 +353,8 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     // With h_resident = 2, z and r of the H-solve also stay on chip, in
     // tensor memory, when every thread's march chunks fit its 16 slots
     // (tm_slots); the TMEM kernel then runs alone on each SM.
+    const bool want_s = P.s_resident != 0;
+    P.s_resident = 0;
     if (P.resident) {
         const int want = P.resident;
         P.resident = 0;
@@ -365,15 +367,22 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
             const size_t rsz = std::max(rs, smem);
             const int elems16 = prec == P_FP32 ? 4 : 8;
             const bool tm = want == 2 && blocks <= h->nsm && tm_slots(h->nx / elems16, h->ny, blocks) <= kTmSlots;
+            // the TMEM kernel's CGNR on S also runs resident (MODE_SOLVE) when
+            // every block owns two rows or more and p fits with two halo
+            // rows on each side
+            const size_t rs4 = (size_t)(rows + 4) * (size_t)h->nx * sizeof(float);
+            const bool sres = want_s && P.mode == MODE_SOLVE && h->ny / blocks >= 2 && rs4 <= (size_t)optin;
             for (int variant = tm ? 2 : 1; variant >= 1 && !P.resident; --variant) {
                 const void *kr = variant == 2 ? kernel_2d5_tm(prec, P.ur_dd) : kernel_2d5_res(prec, P.ur_dd);
-                if (!kr || rsz > (size_t)optin) continue;
-                CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsz));
+                const size_t need = variant == 2 && sres ? std::max(rs4, smem) : rsz;
+                if (!kr || need > (size_t)optin) continue;
+                CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
                 int per_sm_r = 0;
-                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, kr, kThreadsHost, rsz));
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, kr, kThreadsHost, need));
                 if ((long long)per_sm_r * h->nsm >= blocks && (variant == 1 || per_sm_r == 1)) {
                     P.resident = variant;
-                    smem = rsz;
+                    P.s_resident = variant == 2 && sres;
+                    smem = need;
                     k = kr;
                 }
             }
@@ -389,6 +398,7 @@ gadi_status launch(gadi_handle *h, int prec, Params &P, int max_blocks, cudaStre
     CK(cudaMemsetAsync(h->d_bar, 0, 64, st));
     CK(cudaMemsetAsync(h->d_abort, 0, 64, st));
     CK(cudaMemsetAsync(h->d_ctl, 0, sizeof(Ctl), st));
+    fill_coef_sets(P);
     void *args[] = {&P};
     CK(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreadsHost), args, smem, st));
     if (blocks_out) *blocks_out = blocks;
@@ -459,6 +469,7 @@ void fill_inner(gadi_handle *h, Params &P, int prec, double alpha, double omega)
         P.sval = (const char *)h->d_opval + nn * eb;
         P.tval = (const char *)h->d_opval + 2 * nn * eb;
     }
+    fill_coef_sets(P);
 }
 
 __global__ void k_nonfinite(const double *v, long long n, int *flag)
@@ -581,6 +592,7 @@ gadi_status opts_check(const gadi_opts &o)
     if (!(o.tol_h >= 0) || !(o.tol_s >= 0) || o.maxit_inner < 0 || o.inner_stag < 0 || o.outer_stag_window < 0)
         return GADI_ERR_INVALID;
     if (o.h_resident < 0 || o.h_resident > 2) return GADI_ERR_INVALID;
+    if (o.s_resident != 0 && o.s_resident != 1) return GADI_ERR_INVALID;
     if (o.u_r != GADI_FP64 && o.u_r != GADI_FP64X2) return GADI_ERR_INVALID;
     return GADI_OK;
 }
@@ -610,6 +622,7 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     // 12.0 vs 13.2 us per iteration) and slower for BF16 (17.6 vs 16.3)
     o->h_resident = (u_low == GADI_BF16) ? 1 : 2;
     o->u_r = GADI_FP64;
+    o->s_resident = 1;
 }
 
 const char *gadi_last_error(void) { return g_last_error; }
@@ -838,6 +851,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
     P.outer_win = o.outer_stag_window;
     P.pointwise = o.s_pointwise;
     P.resident = o.h_resident;
+    P.s_resident = o.s_resident; // a request; launch() keeps it only where it applies
     P.ur_dd = o.u_r == GADI_FP64X2;
     CK(cudaEventRecord(h->ev0, st));
     int blocks = 0;
@@ -864,6 +878,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
         stats->alpha = alpha;
         stats->restarts = 0;
         stats->h_resident = P.resident;
+        stats->s_resident = P.s_resident;
     }
     return (gadi_status)c.status;
 }
@@ -1161,6 +1176,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.alpha = alpha[u / nrhs];
             S.restarts = 0;
             S.h_resident = 0;
+            S.s_resident = 0;
         }
     }
     return worst;

@@ -99,9 +99,6 @@ __device__ __forceinline__ C stencil_at(C d, const C (&c)[6], C e, C xc, C xw, C
     return s;
 }
 
-template <class C> struct Coef7 {
-    C d, c[6], e;
-};
 
 // The complex class's imaginary diagonal at element v of the chunk that
 // starts at element g (two elements per grid point): the scalar e of the
@@ -929,6 +926,17 @@ struct PhS2 {
 // ---------------------------------------------------------------------------
 // stencil implementation of the phase interface
 // ---------------------------------------------------------------------------
+// the coefficient set k (0 H, 1 S, 2 S^T) of the launch in compute type C
+template <class C> __device__ __forceinline__ const Coef7<C> &coef_set(const Params &p, int k);
+template <> __device__ __forceinline__ const Coef7<float> &coef_set<float>(const Params &p, int k)
+{
+    return k == 0 ? p.hf : (k == 1 ? p.sf : p.tf);
+}
+template <> __device__ __forceinline__ const Coef7<double> &coef_set<double>(const Params &p, int k)
+{
+    return k == 0 ? p.hd : (k == 1 ? p.sd : p.td);
+}
+
 // DD: the residual phase in double-FP64 (u_r ~ u^2); a separate
 // instantiation, so the FP64-residual kernels carry none of its code
 template <int KIND, int PREC, int WI, int WR, bool DD = false>
@@ -949,24 +957,20 @@ struct StencilImpl {
     VGrid vg;
     int ne, ny, nz;
     Coef7<double> ca;
-    Coef7<C> ch, cs, ct;
+    // H, S and S^T in the compute type, read where they are used from the
+    // launch parameters (constant memory) rather than held in registers
+    // for the whole persistent kernel
+    const Coef7<C> &ch, &cs, &ct;
 
-    __device__ StencilImpl(const Params &p, VGrid g) : P(p), vg(g)
+    __device__ StencilImpl(const Params &p, VGrid g)
+        : P(p), vg(g), ch(coef_set<C>(p, 0)), cs(coef_set<C>(p, 1)), ct(coef_set<C>(p, 2))
     {
         ne = p.nx * K;
         ny = p.ny;
         nz = D3 ? p.nz : 1;
         ca.d = p.co.a_d; ca.e = p.co.a_e;
-        ch.d = (C)p.co.h_d; ch.e = C(0);
-        cs.d = (C)p.co.s_d; cs.e = (C)p.co.s_e;
-        ct.d = (C)p.co.t_d; ct.e = (C)p.co.t_e;
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            ca.c[k] = p.co.a_c[k];
-            ch.c[k] = (C)p.co.h_c[k];
-            cs.c[k] = (C)p.co.s_c[k];
-            ct.c[k] = (C)p.co.t_c[k];
-        }
+        for (int k = 0; k < 6; k++) ca.c[k] = p.co.a_c[k];
     }
 
     __device__ static unsigned char *warp_smem()
@@ -1597,15 +1601,18 @@ struct StencilImpl {
             acc[0] = acc[1] = AT(0);
         }
     }
-    // z of the own rows from TMEM to global memory (end of the H-solve)
-    __device__ void h_flush_tm() const
+    // one TMEM set of the own rows (which: 0 z / y, 1 r / t) to global
+    // memory at dst; edges: only the rows the neighbours' halo needs
+    // (edge_rows 1: the slab's first and last row; 2: its first two and last
+    // two)
+    __device__ void tm_flush(int which, S *dst, int edge_rows) const
     {
         if constexpr (TM_OK) {
             constexpr int W = WI, U = 4;
             int ya, yb;
             res_rows(ya, yb);
-            const int nxw = ne / W;
-            const ResMap m = res_map(yb - ya, nxw);
+            const int R = yb - ya, nxw = ne / W;
+            const ResMap m = res_map(R, nxw);
             for (int cp = 0; cp < m.ncp; ++cp) {
                 const int cx = m.cx0 + cp * (int)blockDim.x;
                 const bool col = m.act && cx < nxw;
@@ -1617,20 +1624,422 @@ struct StencilImpl {
                     for (int u = 0; u < U; u++) w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
 #pragma unroll
                     for (int u = 0; u < U; u++)
-                        if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, 0), w[u]);
+                        if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, which), w[u]);
                     tmem_wait_ld<U>(w);
 #pragma unroll
                     for (int u = 0; u < U; u++) {
-                        if (col && m.r0 + s0 + u < m.r1) {
+                        const int row = m.r0 + s0 + u;
+                        if (col && row < m.r1 && (edge_rows == 0 || row < edge_rows || row >= R - edge_rows)) {
                             S zv[W];
                             from_words<W>(w[u], zv);
-                            VecIO<S, W>::store((S *)P.z + ((size_t)(ya + m.r0 + s0 + u) * ne + x0), zv);
+                            VecIO<S, W>::store(dst + ((size_t)(ya + row) * ne + x0), zv);
                         }
                     }
                 }
             }
         }
     }
+    __device__ void h_flush_tm(bool edges_only) const { tm_flush(0, (S *)P.z, edges_only ? 1 : 0); }
+
+    // ---- CGNR on S resident: p in shared memory, t and y in TMEM ----
+    // The TMEM kernel's S-solve for blocks of two rows or more.  The slab
+    // holds p (during s0: g = fl_s(gamma z)) of the rows ya - 2 .. yb + 1
+    // (slot = row - ya + 2): u = fl_s(S p) is never stored but recomputed
+    // where it is needed, from p with the owner's operations, so the S^T u
+    // of a slab row needs p two rows out.  The halo rows of p are
+    // recomputed from the neighbours' t (p = fl_s(t + beta p_old), the
+    // induction of the H-solve); every block publishes t of its first two
+    // and last two rows.  t takes the TMEM slots of r, y those of z.  Same
+    // operations in the same order as the streaming phases PhS0-PhS2.
+    __device__ bool s_edge(int row, int R, int ya, int yb) const
+    {
+        return (row < 2 && ya > 0) || (row >= R - 2 && yb < ny);
+    }
+    // s0: g = fl_s(gamma z) on the slab (halo rows from the neighbours'
+    // published z; own rows from TMEM if z_tm, else from global memory),
+    // then t = fl_s(S^T g), acc = t.t
+    __device__ GADI_RES_FN void s0_tm(C gamma, bool z_tm, AT (&acc)[2]) const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI, U = 4;
+            using A2 = typename InnerAr<PREC>::T;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            float *sp = res_smem();
+            // slab rows outside the grid hold zeros (g and p vanish there)
+            if (ya == 0)
+                for (int i = threadIdx.x; i < 2 * ne; i += blockDim.x) sp[i] = 0.f;
+            if (yb == ny)
+                for (int i = threadIdx.x; i < 2 * ne; i += blockDim.x) sp[(size_t)(R + 2) * ne + i] = 0.f;
+            const S *z = (const S *)P.z;
+            for (int i = threadIdx.x; i < 2 * nxw; i += blockDim.x) {
+                const bool lo = i < nxw;
+                if (lo ? ya == 0 : yb == ny) continue;
+                const int c = lo ? i : i - nxw, row = lo ? -1 : R;
+                S zv[W];
+                VecIO<S, W>::load(z + ((long long)(ya + row) * ne + (long long)c * W), zv);
+                g_chunk<W>(gamma, zv, sp + (size_t)(row + 2) * ne + (size_t)c * W);
+            }
+            const ResMap m = res_map(R, nxw);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const int sb = cp * m.rmax;
+                for (int s0 = 0; s0 < m.rmax; s0 += U) {
+                    unsigned w[U][4];
+#pragma unroll
+                    for (int u = 0; u < U; u++) w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
+                    if (z_tm) {
+#pragma unroll
+                        for (int u = 0; u < U; u++)
+                            if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, 0), w[u]);
+                        tmem_wait_ld<U>(w);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int row = m.r0 + s0 + u;
+                        if (col && row < m.r1) {
+                            S zv[W];
+                            if (z_tm)
+                                from_words<W>(w[u], zv);
+                            else
+                                VecIO<S, W>::load(z + ((size_t)(ya + row) * ne + x0), zv);
+                            g_chunk<W>(gamma, zv, sp + (size_t)(row + 2) * ne + x0);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            AT a = AT(0);
+            s_march01<true>(a);
+            acc[0] = a;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    template <int W>
+    __device__ static void g_chunk(C gamma, const S (&zv)[W], float *pp)
+    {
+        using A2 = typename InnerAr<PREC>::T;
+        float4 *d4 = reinterpret_cast<float4 *>(pp);
+#pragma unroll
+        for (int v = 0; v < W; v += 4) {
+            float4 t;
+            t.x = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v]))));
+            t.y = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 1]))));
+            t.z = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 2]))));
+            t.w = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 3]))));
+            d4[v / 4] = t;
+        }
+    }
+    // s1: p = fl_s(t + beta p_old) (p = t at j = 0) on the slab, then
+    // acc = u.u with u = fl_s(S p) on the own rows
+    __device__ GADI_RES_FN void s1_tm(int j, C beta, AT (&acc)[2]) const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI, U = 4;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            float *sp = res_smem();
+            const S *t = (const S *)P.r;
+            const bool first = j == 0;
+            // halo rows -2, -1, R, R + 1 inside the grid: the neighbours' t
+            const int nh = 4 * nxw;
+            for (int i0 = threadIdx.x; i0 < nh; i0 += U * (int)blockDim.x) {
+                S tv[U][W];
+                int rowu[U], cu[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int i = i0 + u * (int)blockDim.x;
+                    rowu[u] = -100;
+                    if (i < nh) {
+                        const int k = i / nxw, c = i - k * nxw, row = k < 2 ? k - 2 : R + k - 2;
+                        if (ya + row >= 0 && ya + row < ny) {
+                            rowu[u] = row;
+                            cu[u] = c;
+                            VecIO<S, W>::load(t + ((long long)(ya + row) * ne + (long long)c * W), tv[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (rowu[u] != -100)
+                        p_chunk<W>(first, beta, tv[u], sp + (size_t)(rowu[u] + 2) * ne + (size_t)cu[u] * W);
+            }
+            // own rows: t from TMEM
+            const ResMap m = res_map(R, nxw);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const int sb = cp * m.rmax;
+                for (int s0 = 0; s0 < m.rmax; s0 += U) {
+                    unsigned w[U][4];
+#pragma unroll
+                    for (int u = 0; u < U; u++) w[u][0] = w[u][1] = w[u][2] = w[u][3] = 0u;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (s0 + u < m.rmax) tmem_ld4(tm_addr(sb + s0 + u, 1), w[u]);
+                    tmem_wait_ld<U>(w);
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int row = m.r0 + s0 + u;
+                        if (col && row < m.r1) {
+                            S tv[W];
+                            from_words<W>(w[u], tv);
+                            p_chunk<W>(first, beta, tv, sp + (size_t)(row + 2) * ne + x0);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            AT a = AT(0);
+            s_march01<false>(a);
+            acc[0] = a;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    // the column march of s0 (T_OUT: t = fl_s(S^T g) to TMEM and the edge
+    // rows to global memory, acc = t.t) and of s1 (acc = u.u, u = fl_s(S p))
+    template <bool T_OUT>
+    __device__ void s_march01(AT &acc) const
+    {
+        constexpr int W = WI;
+        using A2 = typename InnerAr<PREC>::T;
+        int ya, yb;
+        res_rows(ya, yb);
+        const int R = yb - ya, nxw = ne / W;
+        const float *sp = res_smem();
+        const ResMap m = res_map(R, nxw);
+        const int lane = threadIdx.x & 31;
+        const Coef7<C> &cf = T_OUT ? ct : cs;
+        for (int cp = 0; cp < m.ncp; ++cp) {
+            const int cx = m.cx0 + cp * (int)blockDim.x;
+            const bool col = m.act && cx < nxw;
+            const int x0 = col ? cx * W : 0;
+            const bool lsh = lane > 0 && cx > 0, rsh = lane < 31 && cx + 1 < nxw;
+            const bool xlo = x0 > 0, xhi = x0 + W < ne;
+            // the slab row above the current one (slot = row + 2)
+            const float *up_p = sp + (size_t)(m.r0 + 3) * ne + x0;
+            S *tg = (S *)P.r + ((size_t)(ya + m.r0) * ne + x0);
+            const int sb = cp * m.rmax;
+            float dn[W], c[W], up[W];
+#pragma unroll
+            for (int v = 0; v < W; v++) dn[v] = c[v] = up[v] = 0.f;
+            if (col) {
+                res_row<W>(up_p - 2 * (size_t)ne, dn);
+                res_row<W>(up_p - (size_t)ne, c);
+            }
+            int left = col ? m.r1 - m.r0 : 0;
+            for (int st = 0; st < m.rmax; ++st) {
+                const bool ok = left > 0;
+                if (ok) res_row<W>(up_p, up);
+                float cl = __shfl_up_sync(0xffffffffu, c[W - 1], 1);
+                float cr = __shfl_down_sync(0xffffffffu, c[0], 1);
+                S o[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) o[v] = PT::st(C(0));
+                if (ok) {
+                    if (!lsh) cl = xlo ? up_p[-(ptrdiff_t)ne - 1] : 0.f;
+                    if (!rsh) cr = xhi ? up_p[-(ptrdiff_t)ne + W] : 0.f;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        const float wv = v > 0 ? c[v - 1] : cl, ev = v + 1 < W ? c[v + 1] : cr;
+                        o[v] = PT::st(stencil_at<A2, C, false, false>(cf.d, cf.c, C(0), c[v], wv, ev, dn[v], up[v],
+                                                                      C(0), C(0), C(0), false));
+                        const C q = PT::ld(o[v]);
+                        acc += (AT)q * (AT)q;
+                    }
+                    if constexpr (T_OUT) {
+                        if (s_edge(m.r0 + st, R, ya, yb)) VecIO<S, W>::store(tg, o);
+                    }
+                }
+                if constexpr (T_OUT) {
+                    unsigned w4[4];
+                    to_words<W>(o, w4);
+                    tmem_st4(tm_addr(sb + st, 1), w4);
+                }
+                --left;
+                up_p += ne;
+                tg += ne;
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    dn[v] = c[v];
+                    c[v] = up[v];
+                }
+            }
+        }
+        if constexpr (T_OUT) tmem_wait_st();
+    }
+    // u = fl_s(S p) at one chunk of slab row k from p rows k - 1, k, k + 1
+    // (lo, mid, hi) and the west / east neighbours of mid; zero outside the
+    // grid's rows
+    template <int W>
+    __device__ void u_chunk(const float (&lo)[W], const float (&mid)[W], const float (&hi)[W], float ml, float mr,
+                            bool inside, float (&u)[W]) const
+    {
+        using A2 = typename InnerAr<PREC>::T;
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+            const float wv = v > 0 ? mid[v - 1] : ml, ev = v + 1 < W ? mid[v + 1] : mr;
+            u[v] = inside ? PT::ld(PT::st(stencil_at<A2, C, false, false>(cs.d, cs.c, C(0), mid[v], wv, ev, lo[v],
+                                                                           hi[v], C(0), C(0), C(0), false)))
+                          : 0.f;
+        }
+    }
+    // u = fl_s(S p) at the single element x of slab row k (p read from the
+    // slab; zero outside the grid)
+    __device__ float u_point(const float *sp, int k, int x, bool inside) const
+    {
+        using A2 = typename InnerAr<PREC>::T;
+        if (!inside || x < 0 || x >= ne) return 0.f;
+        const float *r = sp + (size_t)(k + 2) * ne;
+        const float pw = x > 0 ? r[x - 1] : 0.f, pe = x + 1 < ne ? r[x + 1] : 0.f;
+        return PT::ld(PT::st(stencil_at<A2, C, false, false>(cs.d, cs.c, C(0), r[x], pw, pe, r[x - (ptrdiff_t)ne],
+                                                             r[x + ne], C(0), C(0), C(0), false)));
+    }
+    // s2: y = fl_s(y + a p) (a p at j = 0), t = fl_s(t - a S^T u) with
+    // u = fl_s(S p) recomputed, acc = t.t; t of the edge rows to global
+    __device__ GADI_RES_FN void s2_tm(bool first, C a_, AT (&acc)[2]) const
+    {
+        if constexpr (TM_OK) {
+            constexpr int W = WI;
+            using A2 = typename InnerAr<PREC>::T;
+            int ya, yb;
+            res_rows(ya, yb);
+            const int R = yb - ya, nxw = ne / W;
+            const float *sp = res_smem();
+            const ResMap m = res_map(R, nxw);
+            const int lane = threadIdx.x & 31;
+            AT s2 = AT(0);
+            for (int cp = 0; cp < m.ncp; ++cp) {
+                const int cx = m.cx0 + cp * (int)blockDim.x;
+                const bool col = m.act && cx < nxw;
+                const int x0 = col ? cx * W : 0;
+                const bool lsh = lane > 0 && cx > 0, rsh = lane < 31 && cx + 1 < nxw;
+                const bool xlo = x0 > 0, xhi = x0 + W < ne;
+                // slab row pointer of p at row k: sp + (k + 2) ne + x0
+                const float *pk = sp + (size_t)(m.r0 + 2) * ne + x0; // row r0
+                S *tg = (S *)P.r + ((size_t)(ya + m.r0) * ne + x0);
+                const int sb = cp * m.rmax;
+                unsigned w[2][4]; // y, t of the current step
+#pragma unroll
+                for (int k = 0; k < 2; k++) w[k][0] = w[k][1] = w[k][2] = w[k][3] = 0u;
+                if (!first) tmem_ld4(tm_addr(sb, 0), w[0]);
+                tmem_ld4(tm_addr(sb, 1), w[1]);
+                // p rows i - 1, i, i + 1 and u rows i - 1, i (i = r0)
+                float pa[W], pb[W], pc[W], ua[W], ub[W];
+#pragma unroll
+                for (int v = 0; v < W; v++) pa[v] = pb[v] = pc[v] = ua[v] = ub[v] = 0.f;
+                {
+                    float pz[W]; // p row r0 - 2
+#pragma unroll
+                    for (int v = 0; v < W; v++) pz[v] = 0.f;
+                    if (col) {
+                        res_row<W>(pk - 2 * (size_t)ne, pz);
+                        res_row<W>(pk - (size_t)ne, pa);
+                        res_row<W>(pk, pb);
+                        res_row<W>(pk + ne, pc);
+                    }
+                    // u(r0 - 1) from p(r0 - 2), p(r0 - 1), p(r0)
+                    float ml = __shfl_up_sync(0xffffffffu, pa[W - 1], 1);
+                    float mr = __shfl_down_sync(0xffffffffu, pa[0], 1);
+                    if (col) {
+                        if (!lsh) ml = xlo ? pk[-(ptrdiff_t)ne - 1] : 0.f;
+                        if (!rsh) mr = xhi ? pk[-(ptrdiff_t)ne + W] : 0.f;
+                    }
+                    u_chunk<W>(pz, pa, pb, ml, mr, col && ya + m.r0 - 1 >= 0, ua);
+                    // u(r0) from p(r0 - 1), p(r0), p(r0 + 1)
+                    ml = __shfl_up_sync(0xffffffffu, pb[W - 1], 1);
+                    mr = __shfl_down_sync(0xffffffffu, pb[0], 1);
+                    if (col) {
+                        if (!lsh) ml = xlo ? pk[-1] : 0.f;
+                        if (!rsh) mr = xhi ? pk[W] : 0.f;
+                    }
+                    u_chunk<W>(pa, pb, pc, ml, mr, col, ub);
+                }
+                int left = col ? m.r1 - m.r0 : 0;
+                for (int st = 0; st < m.rmax; ++st) {
+                    const bool ok = left > 0;
+                    const int row = m.r0 + st; // i
+                    // p(i + 2), then u(i + 1) from p(i), p(i + 1), p(i + 2)
+                    float pd[W], uc[W];
+#pragma unroll
+                    for (int v = 0; v < W; v++) pd[v] = 0.f;
+                    if (ok) res_row<W>(pk + 2 * (size_t)ne, pd);
+                    float ml = __shfl_up_sync(0xffffffffu, pc[W - 1], 1);
+                    float mr = __shfl_down_sync(0xffffffffu, pc[0], 1);
+                    if (ok) {
+                        if (!lsh) ml = xlo ? pk[(ptrdiff_t)ne - 1] : 0.f;
+                        if (!rsh) mr = xhi ? pk[(ptrdiff_t)ne + W] : 0.f;
+                    }
+                    u_chunk<W>(pb, pc, pd, ml, mr, ok && ya + row + 1 < ny, uc);
+                    // S^T u at row i: west / east u(i) from the adjacent lanes,
+                    // else recomputed from the slab
+                    float ul = __shfl_up_sync(0xffffffffu, ub[W - 1], 1);
+                    float ur = __shfl_down_sync(0xffffffffu, ub[0], 1);
+                    C q[W];
+#pragma unroll
+                    for (int v = 0; v < W; v++) q[v] = C(0);
+                    if (ok) {
+                        if (!lsh) ul = xlo ? u_point(sp, row, x0 - 1, true) : 0.f;
+                        if (!rsh) ur = xhi ? u_point(sp, row, x0 + W, true) : 0.f;
+#pragma unroll
+                        for (int v = 0; v < W; v++) {
+                            const float wv = v > 0 ? ub[v - 1] : ul, ev = v + 1 < W ? ub[v + 1] : ur;
+                            q[v] = stencil_at<A2, C, false, false>(ct.d, ct.c, C(0), ub[v], wv, ev, ua[v], uc[v], C(0),
+                                                                  C(0), C(0), false);
+                        }
+                    }
+                    tmem_wait_ld<2>(w);
+                    S yv[W], tv[W];
+                    from_words<W>(w[0], yv);
+                    from_words<W>(w[1], tv);
+                    if (ok) {
+#pragma unroll
+                        for (int v = 0; v < W; v++) {
+                            yv[v] = PT::st(first ? A2::mul(a_, pb[v]) : A2::madd(a_, pb[v], PT::ld(yv[v])));
+                            tv[v] = PT::st(A2::madd(-a_, q[v], PT::ld(tv[v])));
+                            const C t2 = PT::ld(tv[v]);
+                            s2 += (AT)t2 * (AT)t2;
+                        }
+                        if (s_edge(row, R, ya, yb)) VecIO<S, W>::store(tg, tv);
+                    }
+                    to_words<W>(yv, w[0]);
+                    to_words<W>(tv, w[1]);
+                    tmem_st4(tm_addr(sb + st, 0), w[0]);
+                    tmem_st4(tm_addr(sb + st, 1), w[1]);
+                    if (st + 1 < m.rmax) {
+                        if (!first) tmem_ld4(tm_addr(sb + st + 1, 0), w[0]);
+                        tmem_ld4(tm_addr(sb + st + 1, 1), w[1]);
+                    }
+                    --left;
+                    pk += ne;
+                    tg += ne;
+#pragma unroll
+                    for (int v = 0; v < W; v++) {
+                        pa[v] = pb[v];
+                        pb[v] = pc[v];
+                        pc[v] = pd[v];
+                        ua[v] = ub[v];
+                        ub[v] = uc[v];
+                    }
+                }
+            }
+            tmem_wait_st();
+            acc[0] = s2;
+            acc[1] = AT(0);
+        } else {
+            acc[0] = acc[1] = AT(0);
+        }
+    }
+    __device__ void s_flush_tm() const { tm_flush(0, (S *)P.y, 0); }
 
     // complex class: S = alpha I + i T (T = sigma I or diag(T_i)),
     // y = fl_s(g / (alpha + i T_i)) pointwise

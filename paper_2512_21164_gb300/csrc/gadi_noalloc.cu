@@ -175,6 +175,7 @@ extern "C" gadi_status gadi_solve_h_2d_noalloc(int nx, int ny, double alpha, gad
     if ((e = cudaMemcpyAsync(slab[0], rs, eb * (size_t)n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return na_fail(e, "cudaMemcpyAsync");
     void *args[] = {&P};
+    fill_coef_sets(P);
     if ((e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(kThreadsNA), args, smem, st)) != cudaSuccess)
         return na_fail(e, "cudaLaunchCooperativeKernel");
     Ctl hc;

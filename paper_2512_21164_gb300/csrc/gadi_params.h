@@ -23,6 +23,12 @@ enum : int {
     MODE_APPLY = 4     // y = Op x in FP64
 };
 
+// A 7-point coefficient set: centre d, neighbours c (W, E, S, N, B, T) and
+// the complex class's imaginary diagonal e.
+template <class C> struct Coef7 {
+    C d, c[6], e;
+};
+
 // Device-written results of a launch.
 struct Ctl {
     int status;
@@ -50,6 +56,10 @@ struct Params {
     int nx, ny, nz;
     long long npts, nelem; // nelem = doubles per outer vector
     Coefs co;
+    // H, S, S^T of `co` as sets in FP32 (the FP32/BF16 compute type) and
+    // FP64 (H's e = 0); filled from `co` by fill_coef_sets before launch
+    Coef7<float> hf, sf, tf;
+    Coef7<double> hd, sd, td;
     // CSR (device arrays)
     const int *rowptr, *col;
     const double *aval;                 // A
@@ -67,7 +77,10 @@ struct Params {
     // control
     double tol, tol_h, tol_s;
     int maxit, maxit_inner, inner_stag, outer_win, pointwise, first_y_null;
-    int resident;  // 1: the H-solve keeps p in shared memory (2D, FP32/BF16)
+    int resident;  // 1: the H-solve keeps p in shared memory (2D, FP32/BF16);
+                   // 2: also z and r in tensor memory
+    int s_resident; // with resident = 2 in MODE_SOLVE: CGNR on S with p in
+                    // shared memory and t, y in tensor memory (blocks of >= 2 rows)
     int ur_dd;     // 1: the residual in double-FP64 (u_r ~ u^2)
     // complex class with a per-point imaginary diagonal T = diag(sig) (FP64,
     // one value per grid point; null: the scalar sigma of the coefficients);
@@ -80,6 +93,28 @@ struct Params {
     unsigned long long *bar;
     int *abort_flag;
 };
+
+// Derive the coefficient sets hf/sf/tf and hd/sd/td from P.co (host side,
+// before every launch; FP32 by round to nearest, as a device conversion).
+inline void fill_coef_sets(Params &P)
+{
+    const Coefs &c = P.co;
+    P.hd.d = c.h_d; P.hd.e = 0.0;
+    P.sd.d = c.s_d; P.sd.e = c.s_e;
+    P.td.d = c.t_d; P.td.e = c.t_e;
+    for (int k = 0; k < 6; k++) {
+        P.hd.c[k] = c.h_c[k];
+        P.sd.c[k] = c.s_c[k];
+        P.td.c[k] = c.t_c[k];
+    }
+    const Coef7<double> *d[3] = {&P.hd, &P.sd, &P.td};
+    Coef7<float> *f[3] = {&P.hf, &P.sf, &P.tf};
+    for (int i = 0; i < 3; i++) {
+        f[i]->d = (float)d[i]->d;
+        f[i]->e = (float)d[i]->e;
+        for (int k = 0; k < 6; k++) f[i]->c[k] = (float)d[i]->c[k];
+    }
+}
 
 // One batched launch: units (system, right-hand side) taken from a queue by
 // groups of `gsize` blocks.  Per-group state is strided by group index.

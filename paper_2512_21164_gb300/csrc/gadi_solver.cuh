@@ -221,7 +221,11 @@ struct CsrImpl {
     // (the SM-resident H-solve exists for the 2D stencil class only)
     struct ResRing {};
     static constexpr bool TMEM = false;
-    __device__ void hflush() const {}
+    __device__ void hflush(bool) const {}
+    __device__ void s0r(C, bool, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
+    __device__ void s1r(int, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
+    __device__ void s2r(bool, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
+    __device__ void sflush() const {}
     __device__ void h1r(int, C, AT (&acc)[2]) const { acc[0] = acc[1] = AT(0); }
     __device__ void h2pre(bool, ResRing &) const {}
     __device__ void h2r(bool, C, AT (&acc)[2], ResRing &) const { acc[0] = acc[1] = AT(0); }
@@ -312,7 +316,11 @@ struct StencilAdapter {
         else
             si.h2_res(first, a, acc, q);
     }
-    __device__ void hflush() const { si.h_flush_tm(); }
+    __device__ void hflush(bool edges_only) const { si.h_flush_tm(edges_only); }
+    __device__ void s0r(C gamma, bool z_tm, AT (&acc)[2]) const { si.s0_tm(gamma, z_tm, acc); }
+    __device__ void s1r(int j, C beta, AT (&acc)[2]) const { si.s1_tm(j, beta, acc); }
+    __device__ void s2r(bool first, C a, AT (&acc)[2]) const { si.s2_tm(first, a, acc); }
+    __device__ void sflush() const { si.s_flush_tm(); }
 };
 
 // ---------------------------------------------------------------------------
@@ -423,17 +431,67 @@ struct Runner {
         }
         if constexpr (Impl::TMEM) {
             // z leaves tensor memory; the S-solve reads it across blocks
+            // (the resident S-solve only the rows the neighbours' halo
+            // needs: it takes its own rows from tensor memory)
             if (its > 0) {
-                I.hflush();
+                I.hflush(P.s_resident && P.mode == MODE_SOLVE);
                 if (!gs.sync()) return -1;
             }
         }
         return its;
     }
 
-    // S-solve from z (P.z) into y (P.y).  Returns iterations or -1.
-    __device__ int s_loop(C gamma)
+    // CGNR on S with p in shared memory and t, y in tensor memory (the
+    // TMEM kernel, P.s_resident); z_tm: z of the own rows is in tensor
+    // memory (the H-solve ran), else in global memory
+    __device__ int s_loop_res(C gamma, bool z_tm)
     {
+        const long long m = P.nelem;
+        AT acc[2], sum[2];
+        I.s0r(gamma, z_tm, acc);
+        if (!reduce(acc, sum)) return -1;
+        C tt = (C)sum[0];
+        if (tt == C(0)) {
+            phase_zero<PREC>(P.y, m, I.vg);
+            return gs.sync() ? 0 : -1;
+        }
+        const C thr = floor_to<C>(P.tol_s * P.tol_s * (double)tt);
+        C beta = C(0), best = tt;
+        int since = 0, its = 0;
+        for (int j = 0; j < P.maxit_inner; ++j) {
+            I.s1r(j, beta, acc);
+            if (!reduce(acc, sum)) return -1;
+            const C a = A::div(tt, (C)sum[0]);
+            I.s2r(j == 0, a, acc);
+            if (!reduce(acc, sum)) return -1;
+            const C tn = (C)sum[0];
+            its = j + 1;
+            if (tn <= thr) break;
+            if (!(tn == tn)) break;
+            if (tn < best) {
+                best = tn;
+                since = 0;
+            } else if (P.inner_stag > 0 && ++since >= P.inner_stag) {
+                break;
+            }
+            beta = A::div(tn, tt);
+            tt = tn;
+        }
+        // y leaves tensor memory; the next residual reads it across blocks
+        if (its > 0) {
+            I.sflush();
+            if (!gs.sync()) return -1;
+        }
+        return its;
+    }
+
+    // S-solve from z (P.z) into y (P.y).  Returns iterations or -1.
+    // z_tm: the H-solve left z of the own rows in tensor memory.
+    __device__ int s_loop(C gamma, bool z_tm = false)
+    {
+        if constexpr (Impl::TMEM) {
+            if (P.s_resident) return s_loop_res(gamma, z_tm);
+        }
         const long long m = P.nelem;
         if (Impl::K == 2 && P.pointwise) {
             I.s_pointwise(gamma);
@@ -539,7 +597,7 @@ struct Runner {
             const int a = h_loop((C)dsum[1]);
             if (a < 0) return;
             ih += a;
-            const int b = s_loop(gamma);
+            const int b = s_loop(gamma, a > 0);
             if (b < 0) return;
             is += b;
         }

@@ -214,7 +214,7 @@ def test_resident_h_solve_matches_streaming_and_oracle(prec, max_blocks):
     res, xs = {}, {}
     for hr in (2, 1, 0):
         st, sg, xg, hg = _gpu_solve(p, b, alpha, 1.0, prec, 1e-10, 3000, max_blocks=max_blocks,
-                                    h_resident=hr)
+                                    h_resident=hr, s_resident=0)
         assert st == G.OK, G.status_str(st)
         assert sg["h_resident"] == hr and sg["blocks"] == max_blocks
         rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
@@ -259,7 +259,7 @@ def test_tmem_h_solve_same_bits_as_shared_memory_form(prec, nx, ny, blocks):
         for hr in (2, 1):
             x = torch.zeros_like(b)
             st, s = H.solve(b, x, 4 * a0, 0.0, prec, 1e-12, 4, tol_h=th, tol_s=ts, max_blocks=blocks,
-                            h_resident=hr, check=False)
+                            h_resident=hr, s_resident=0, check=False)
             assert st in (G.OK, G.NOT_CONVERGED), G.status_str(st)
             out[hr] = (s, x.cpu().numpy())
     want = 2 if _tm_slots(nx, ny, prec, blocks) <= 16 else 1
@@ -269,12 +269,60 @@ def test_tmem_h_solve_same_bits_as_shared_memory_form(prec, nx, ny, blocks):
         assert out[2][0][key] == out[1][0][key]
 
 
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("nx,ny,blocks", [(48, 40, 16), (48, 32, 16), (48, 16, 16), (8, 400, 16),
+                                          (2560, 200, 16)])
+def test_resident_cgnr_matches_streaming(prec, nx, ny, blocks):
+    """CGNR on S with p in shared memory and t, y in tensor memory
+    (s_resident = 1, taken with the tensor-memory H-solve when every block
+    owns two rows or more; 2560 x 200 FP32 needs more than 16 slots and
+    takes neither) against
+    the streaming S-solve (s_resident = 0): both reach 1e-10, outer
+    iterations within the precision's band, and the small grids against the
+    oracle."""
+    import torch
+    p, xt = conv_diff_2d(nx, 213, ny=ny)
+    a0 = alpha_star(p)
+    th, ts = _tols(prec)
+    out = {}
+    with G.Gadi.from_problem(p) as H:
+        xtd = torch.from_numpy(np.ascontiguousarray(xt)).cuda()
+        b = torch.zeros_like(xtd)
+        H.apply(G.OP_A, xtd, b)
+        r = torch.zeros_like(b)
+        for sr in (1, 0):
+            x = torch.zeros_like(b)
+            st, s = H.solve(b, x, 2 * a0, 1.0, prec, 1e-10, 4000, tol_h=th, tol_s=ts, max_blocks=blocks,
+                            h_resident=2, s_resident=sr)
+            assert st == G.OK, G.status_str(st)
+            H.apply(G.OP_A, x, r)
+            rel = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+            assert rel <= 1e-10
+            out[sr] = (s, x.cpu().numpy())
+    tm = _tm_slots(nx, ny, prec, blocks) <= 16
+    want = 1 if tm and ny // blocks >= 2 else 0
+    assert out[1][0]["s_resident"] == want and out[0][0]["s_resident"] == 0
+    assert out[1][0]["h_resident"] == (2 if tm else 1)
+    o1, o0 = out[1][0]["outer_its"], out[0][0]["outer_its"]
+    assert abs(o1 - o0) <= max(2, BAND[prec] * o0)
+    if nx * ny <= 4096:
+        orc = O.Oracle(p)
+        xo, so = orc.gadi(orc.rhs(xt), 2 * a0, 1.0, prec, tol=1e-10, maxit=4000, tol_h=th, tol_s=ts)
+        assert abs(o1 - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
+        fo = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+        f1 = np.linalg.norm(out[1][1] - xt) / np.linalg.norm(xt)
+        assert f1 <= 10 * fo + 1e-12
+
+
 def test_resident_option_validated():
     p, xt = conv_diff_2d(16, 206)
     b = O.Oracle(p).rhs(xt)
     with G.Gadi.from_problem(p) as H:
         for bad in (3, -1):
             st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, h_resident=bad, check=False)
+            assert st == G.ERR_INVALID
+        for bad in (2, -1):
+            st, _ = H.solve(b, np.zeros(p.nvec), 0.5, 1.0, FP32, 1e-10, 10, s_resident=bad, check=False)
             assert st == G.ERR_INVALID
 
 
