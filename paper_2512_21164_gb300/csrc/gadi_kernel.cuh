@@ -552,6 +552,15 @@ __device__ __forceinline__ void dd_sub_term(double &hi, double &lo, double a, do
     lo = __dadd_rn(lo, __dadd_rn(q, pe));
 }
 
+// x * 2^k is x with k added to its exponent field when x is normal and the
+// result stays normal (then exact); zero, subnormal, infinite and NaN x or a
+// result out of the normal range need the multiplication
+__device__ __forceinline__ bool pow2_shift_ok(double x, int k)
+{
+    const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+    return ex != 0 && ex != 0x7ff && ex + k >= 1 && ex + k <= 0x7fe;
+}
+
 template <int PREC, int W, int K, bool D3, bool DD = false>
 struct PhResidual {
     using PT = Prec<PREC>;
@@ -568,6 +577,7 @@ struct PhResidual {
     double *rlo; // DD: low parts of r (nullable)
     const double *sig = nullptr; // complex class: per-point T (null: cf.e)
     double esign = 1.0;
+    int dpow2 = kNoPow2; // cf.d = 2^dpow2 (see mul_pow2), else kNoPow2
     __device__ void load_own(long long g, Own &o) const
     {
         if (b) VecIO<double, W>::load(b + g, o.v[0]);
@@ -599,11 +609,38 @@ struct PhResidual {
             }
         } else {
             double ax[W];
+            // with a power-of-two centre (the 2D 5-point Laplacian's 4) the
+            // product cf.d x is an exponent shift, exact and bit-identical,
+            // taken on the integer pipe when the whole warp's points allow it
+            bool shift = false;
+            if constexpr (K == 1) {
+                bool ok = dpow2 != kNoPow2;
 #pragma unroll
-            for (int v = 0; v < W; v++)
-                ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c, K == 2 ? pt_e_exact(sig, esign, g, v, cf.e) : 0.0,
-                                                          c[v], w[v], e[v], s[v], n[v], bb[v], t[v], c[v ^ (K - 1)],
-                                                          (v & 1) != 0);
+                for (int v = 0; v < W; v++) ok = ok && pow2_shift_ok(c[v], dpow2);
+                shift = __all_sync(__activemask(), ok); // out() runs on the strip's active lanes
+            }
+            if (shift) {
+#pragma unroll
+                for (int v = 0; v < W; v++) {
+                    double q = __longlong_as_double(__double_as_longlong(c[v]) + ((long long)dpow2 << 52));
+                    q = fma(cf.c[0], w[v], q);
+                    q = fma(cf.c[1], e[v], q);
+                    q = fma(cf.c[2], s[v], q);
+                    q = fma(cf.c[3], n[v], q);
+                    if constexpr (D3) {
+                        q = fma(cf.c[4], bb[v], q);
+                        q = fma(cf.c[5], t[v], q);
+                    }
+                    ax[v] = q;
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < W; v++)
+                    ax[v] = stencil_at<A, double, D3, K == 2>(cf.d, cf.c,
+                                                              K == 2 ? pt_e_exact(sig, esign, g, v, cf.e) : 0.0,
+                                                              c[v], w[v], e[v], s[v], n[v], bb[v], t[v],
+                                                              c[v ^ (K - 1)], (v & 1) != 0);
+            }
             if (b == nullptr) { // operator application: xo = Op x
                 VecIO<double, W>::store(xo + g, ax);
                 return;
@@ -991,6 +1028,7 @@ struct StencilImpl {
     {
         double a[2] = {0.0, 0.0}; // a[1]: the float pair (hi, lo), both +0
         PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out, P.sig, P.sig_a};
+        ph.dpow2 = P.ad_pow2;
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
         acc[1] = (double)__int_as_float(__double2hiint(a[1])) + (double)__int_as_float(__double2loint(a[1]));
@@ -998,6 +1036,7 @@ struct StencilImpl {
     __device__ void apply(const double *x, double *yout) const
     {
         PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca, nullptr, P.sig, P.sig_a};
+        ph.dpow2 = P.ad_pow2;
         double a[2] = {0.0, 0.0};
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
     }

@@ -60,6 +60,9 @@ struct Params {
     // FP64 (H's e = 0); filled from `co` by fill_coef_sets before launch
     Coef7<float> hf, sf, tf;
     Coef7<double> hd, sd, td;
+    // k if A's centre coefficient co.a_d is 2^k (|k| < 1000), else kNoPow2:
+    // the residual then forms a_d x by adding k to x's exponent
+    int ad_pow2;
     // CSR (device arrays)
     const int *rowptr, *col;
     const double *aval;                 // A
@@ -94,11 +97,23 @@ struct Params {
     int *abort_flag;
 };
 
-// Derive the coefficient sets hf/sf/tf and hd/sd/td from P.co (host side,
-// before every launch; FP32 by round to nearest, as a device conversion).
+constexpr int kNoPow2 = 1 << 30;
+
+// Derive the coefficient sets hf/sf/tf and hd/sd/td and ad_pow2 from P.co
+// (host side, before every launch; FP32 by round to nearest, as a device
+// conversion).
 inline void fill_coef_sets(Params &P)
 {
     const Coefs &c = P.co;
+    P.ad_pow2 = kNoPow2;
+    {
+        uint64_t u;
+        static_assert(sizeof(double) == sizeof(uint64_t), "binary64");
+        __builtin_memcpy(&u, &c.a_d, 8);
+        const int ex = (int)((u >> 52) & 0x7ff);
+        // a positive normal power of two: sign 0, fraction 0
+        if ((u >> 63) == 0 && (u & 0xfffffffffffffull) == 0 && ex != 0 && ex != 0x7ff) P.ad_pow2 = ex - 1023;
+    }
     P.hd.d = c.h_d; P.hd.e = 0.0;
     P.sd.d = c.s_d; P.sd.e = c.s_e;
     P.td.d = c.t_d; P.td.e = c.t_e;
