@@ -280,6 +280,7 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
         "wall_s": t_wall,
+        "step_s": per,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(p, xt, alpha, mixed_stats, args.cpu_outer)
