@@ -1485,14 +1485,24 @@ struct StencilImpl {
                 if (yb == ny)
                     for (int i = threadIdx.x; i < ne; i += blockDim.x) sp[(size_t)(R + 1) * ne + i] = 0.f;
             }
-            // halo rows ya - 1 and yb (smem rows 0 and R + 1)
-            for (int i = threadIdx.x; i < 2 * nxw; i += blockDim.x) {
-                const bool lo = i < nxw;
-                if (lo ? ya == 0 : yb == ny) continue;
-                const int c = lo ? i : i - nxw, row = lo ? -1 : R;
-                S rv[W];
-                VecIO<S, W>::load(r + ((long long)(ya + row) * ne + (long long)c * W), rv);
-                p_chunk<W>(first, beta, rv, sp + (size_t)(row + 1) * ne + (size_t)c * W);
+            // halo rows ya - 1 and yb (smem rows 0 and R + 1): the loads of a
+            // thread's first HU chunks are issued before the own rows' work
+            // and used after it
+            constexpr int HU = 2;
+            S hv[HU][W];
+            int hc[HU];
+#pragma unroll
+            for (int u = 0; u < HU; u++) {
+                const int i = (int)threadIdx.x + u * (int)blockDim.x;
+                hc[u] = -1;
+                if (i < 2 * nxw) {
+                    const bool lo = i < nxw;
+                    if (!(lo ? ya == 0 : yb == ny)) {
+                        hc[u] = i;
+                        VecIO<S, W>::load(r + ((long long)(lo ? ya - 1 : yb) * ne + (long long)(lo ? i : i - nxw) * W),
+                                          hv[u]);
+                    }
+                }
             }
             // own rows, in the march's thread map
             const ResMap m = res_map(R, nxw);
@@ -1534,6 +1544,21 @@ struct StencilImpl {
                         }
                     }
                 }
+            }
+#pragma unroll
+            for (int u = 0; u < HU; u++) {
+                if (hc[u] >= 0) {
+                    const bool lo = hc[u] < nxw;
+                    p_chunk<W>(first, beta, hv[u], sp + (size_t)(lo ? 0 : R + 1) * ne + (size_t)(lo ? hc[u] : hc[u] - nxw) * W);
+                }
+            }
+            for (int i = (int)threadIdx.x + HU * (int)blockDim.x; i < 2 * nxw; i += blockDim.x) {
+                const bool lo = i < nxw;
+                if (lo ? ya == 0 : yb == ny) continue;
+                const int c = lo ? i : i - nxw, row = lo ? -1 : R;
+                S rv[W];
+                VecIO<S, W>::load(r + ((long long)(ya + row) * ne + (long long)c * W), rv);
+                p_chunk<W>(first, beta, rv, sp + (size_t)(row + 1) * ne + (size_t)c * W);
             }
             if (first) tmem_wait_st();
             __syncthreads();
