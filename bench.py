@@ -616,7 +616,7 @@ def run_reference(args):
     p, xt = config2(args.grid)
     alpha = ALPHA_FACTOR * alpha_star(p)
     # scaled to the outer iterations the mixed solve needs on this workload
-    # (2586, measured on GB300); the arm times the oracle's cost per outer
+    # (2585, measured on GB300); the arm times the oracle's cost per outer
     # iteration on a bounded sample, not a full oracle solve
     counts = {"outer_its": args.ref_outer}
     vals = []
@@ -649,7 +649,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-outer", type=int, default=1)
-    ap.add_argument("--ref-outer", type=int, default=2586)
+    ap.add_argument("--ref-outer", type=int, default=2585)
     ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
                     help="run one solve capped at --maxit outer iterations (for ncu) and exit")
     ap.add_argument("--grids", default=None, help="paper2d / paper3d / paperc: comma-separated grid sizes")
