@@ -975,8 +975,13 @@ template <> __device__ __forceinline__ const Coef7<double> &coef_set<double>(con
 }
 
 // DD: the residual phase in double-FP64 (u_r ~ u^2); a separate
-// instantiation, so the FP64-residual kernels carry none of its code
-template <int KIND, int PREC, int WI, int WR, bool DD = false>
+// instantiation, so the FP64-residual kernels carry none of its code.
+// CMODE: how the H, S, S^T coefficients are held -- 0: copies of the
+// launch parameters' sets, 1: read from the launch parameters where they are
+// used (the tensor-memory kernel, whose registers are short), 2: converted
+// from the FP64 coefficients once (the 2D streaming kernel, measured fastest
+// so at 4096^2).
+template <int KIND, int PREC, int WI, int WR, bool DD = false, int CMODE = 0>
 struct StencilImpl {
     using PT = Prec<PREC>;
     using S = typename PT::S;
@@ -994,10 +999,9 @@ struct StencilImpl {
     VGrid vg;
     int ne, ny, nz;
     Coef7<double> ca;
-    // H, S and S^T in the compute type, read where they are used from the
-    // launch parameters (constant memory) rather than held in registers
-    // for the whole persistent kernel
-    const Coef7<C> &ch, &cs, &ct;
+    // H, S and S^T in the compute type (see CMODE)
+    using CoefSet = std::conditional_t<CMODE == 1, const Coef7<C> &, Coef7<C>>;
+    CoefSet ch, cs, ct;
 
     __device__ StencilImpl(const Params &p, VGrid g)
         : P(p), vg(g), ch(coef_set<C>(p, 0)), cs(coef_set<C>(p, 1)), ct(coef_set<C>(p, 2))
@@ -1005,6 +1009,17 @@ struct StencilImpl {
         ne = p.nx * K;
         ny = p.ny;
         nz = D3 ? p.nz : 1;
+        if constexpr (CMODE == 2) {
+            ch.d = (C)p.co.h_d; ch.e = C(0);
+            cs.d = (C)p.co.s_d; cs.e = (C)p.co.s_e;
+            ct.d = (C)p.co.t_d; ct.e = (C)p.co.t_e;
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                ch.c[k] = (C)p.co.h_c[k];
+                cs.c[k] = (C)p.co.s_c[k];
+                ct.c[k] = (C)p.co.t_c[k];
+            }
+        }
         ca.d = p.co.a_d; ca.e = p.co.a_e;
 #pragma unroll
         for (int k = 0; k < 6; k++) ca.c[k] = p.co.a_c[k];

@@ -623,7 +623,8 @@ struct Runner {
 template <int KIND, int PREC, int WI, int WR, int RES = 0, bool DD = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_stencil_kernel(const __grid_constant__ Params P)
 {
-    using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR, DD>, RES>;
+    using Ad = StencilAdapter<StencilImpl<KIND, PREC, WI, WR, DD, RES == 2 ? 1 : (KIND == K_2D5 && RES == 0 ? 2 : 0)>,
+                              RES>;
     Ad I(P, whole_grid());
     if constexpr (Ad::TMEM) {
         __shared__ unsigned s_tm;
