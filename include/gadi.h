@@ -140,7 +140,7 @@ typedef struct {
     double *hist;          /* optional HOST array of maxit+1 doubles: relres
                               per outer iteration                           */
     int batch_group;       /* gadi_solve_batched: blocks per group (0 = 8)  */
-    int alpha_restarts;    /* Sec. 4.3 step 3: on STAGNATED or DIVERGED,
+    int alpha_restarts;    /* Sec. 4.3: on STAGNATED or DIVERGED,
                               double alpha and continue from the last finite
                               iterate, up to this many times (0 = off)      */
     int h_resident;        /* 2D real class, FP32/BF16, 16-byte aligned rows:
@@ -178,7 +178,7 @@ typedef struct {
     int status;             /* same as the return value                      */
     int blocks;             /* persistent blocks launched                    */
     double alpha;           /* alpha of the last run (after any restarts)    */
-    int restarts;           /* alpha restarts taken (Sec. 4.3 step 3)        */
+    int restarts;           /* alpha restarts taken (Sec. 4.3)               */
     int h_resident;         /* the H-solve taken: 0 streaming, 1 p in shared
                                memory, 2 p in shared and z, r in tensor
                                memory                                        */
@@ -239,14 +239,14 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
                                gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
                                gadi_stats *per_unit);
 
-/* Sec. 4.3, step 2: condition numbers of H = alpha I + M and S = alpha I + N
+/* Sec. 4.3, the check of eq. 4.1: condition numbers of H = alpha I + M and S = alpha I + N
  * from closed forms, for the stencil classes (host only, no GPU work).
  * M's spectrum is the sum of 1D Dirichlet Laplacian spectra plus kappa, so
  * kappa(H) = (alpha + lmax) / (alpha + lmin) exactly.
  * N is normal with eigenvalues i (sum_i 2 c_i cos(j pi h_i)) (i sigma for the
  * complex class), so kappa(S) <= sqrt(alpha^2 + ||N||^2) / alpha, the value
  * returned (an upper bound; equal when N is singular).  CSR: UNSUPPORTED (no
- * cheap estimate; step 2 is then skipped, as Sec. 4.3 allows). */
+ * cheap estimate; the check is then skipped, as Sec. 4.3 allows). */
 gadi_status gadi_condition_numbers(const gadi_problem *prob, double alpha, double *kappa_h, double *kappa_s);
 
 /* Sec. 4.3, steps 2-3: the smallest alpha_out = alpha0 * 2^k (k >= 0, k <= 60)
@@ -304,13 +304,13 @@ gadi_status gadi_step_residual_ur(gadi_handle *h, gadi_prec u_r, gadi_prec u_low
                                   const double *x, const void *y, double *x_out, double *r_out,
                                   double *r_lo_out, void *rs, double *rnorm, void *stream);
 
-/* H-solve (Algorithm 1 line 3): CG on (alpha I + M) z = rs in u_s from z = 0,
+/* H-solve (Algorithm 1, the solve with alpha I + M): CG on (alpha I + M) z = rs in u_s from z = 0,
  * until ||res|| <= tol ||rs|| (tol = 0: exactly maxit steps), or `stag` steps
  * without a new minimum (0 = off).  *its receives the iteration count. */
 gadi_status gadi_step_solve_h(gadi_handle *h, double alpha, gadi_prec u_low, const void *rs,
                               void *z, double tol, int maxit, int stag, int *its, void *stream);
 
-/* S-solve (Algorithm 1 line 4): g = fl_{u_s}((2 - omega) alpha z), then CG on
+/* S-solve (Algorithm 1, the solve with alpha I + N): g = fl_{u_s}((2 - omega) alpha z), then CG on
  * S^T S y = S^T g from y = 0 (t_0 = fl_{u_s}(S^T g)), same stopping rules;
  * pointwise != 0 with the complex class: y = fl_{u_s}(g / (alpha + i sigma)). */
 gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_prec u_low,

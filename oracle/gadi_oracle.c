@@ -307,7 +307,7 @@ void orc_csr_apply(int n, const int *rowptr, const int *col, const double *val,
  * (N is skew: N^T = -N; in the complex case the adjoint S^H = alpha I - i sigma I
  * plays the role of S^T).  The stored coefficients of H and S are rounded to
  * u_s: H's diagonal as fl(alpha + d_M), as a stored matrix H would hold it
- * (Sec. 5.1, "GADI memory consumption").
+ * (Sec. 5.1, on the memory GADI needs).
  * CSR: M = (A + A^T)/2 and N = (A - A^T)/2 are passed in; H = alpha I + M,
  * S = alpha I + N and S^T = alpha I - N are formed in FP64 on M's pattern and
  * their values rounded to u_s. */

@@ -318,7 +318,7 @@ def _problem_struct(p):
 
 
 def condition_numbers(p, alpha):
-    """gadi_condition_numbers (Sec. 4.3 step 2) for a workloads.Problem: (kappa_H, kappa_S bound)."""
+    """gadi_condition_numbers (Sec. 4.3, the condition check of eq. 4.1) for a workloads.Problem: (kappa_H, kappa_S bound)."""
     kh, ks = C.c_double(), C.c_double()
     st = lib().gadi_condition_numbers(C.byref(_problem_struct(p)), float(alpha), C.byref(kh), C.byref(ks))
     if st != OK:

@@ -883,7 +883,7 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
     return (gadi_status)c.status;
 }
 
-// closed-form spectra of the stencil classes (Sec. 4.3 step 2)
+// closed-form spectra of the stencil classes (Sec. 4.3, the condition check)
 bool stencil_spectra(const gadi_problem *p, double *lmin, double *lmax, double *nnorm)
 {
     if (!p || p->kind == GADI_CSR || p->kind < 0 || p->kind > GADI_CSR) return false;
@@ -1005,7 +1005,7 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
         if (stats) *stats = st1;
         return s;
     }
-    // Sec. 4.3 step 3: stop, increase alpha, repeat -- from the last iterate,
+    // Sec. 4.3: on stagnation or divergence, a larger alpha and a new run -- from the last iterate,
     // with the tolerance kept relative to the first residual norm
     gadi_stats acc = st1;
     const double r0 = st1.r0_norm;

@@ -166,7 +166,7 @@ def test_norm2_estimate():
 
 
 def test_alpha_restarts_recover_from_stagnation():
-    """Sec. 4.3 step 3: a BF16 run with a too-small alpha stagnates; with
+    """Sec. 4.3 (a larger alpha after stagnation): a BF16 run with a too-small alpha stagnates; with
     restarts, alpha is doubled from the last iterate until it converges."""
     p, xt = conv_diff_2d(48, 9)
     orc = O.Oracle(p)
