@@ -1429,8 +1429,9 @@ struct StencilImpl {
     // TMEM, z in the slot's first four columns and r in the next four (16
     // bytes each).  Global memory then sees only what other blocks need: r
     // of the slab's first and last row (the neighbours' halo) every
-    // iteration, and z once, when the solve ends.  Same arithmetic as the
-    // L2 variant, so both give the same bits.
+    // iteration, and z once, when the solve ends (all rows; only the first
+    // and last when the resident S-solve follows, which takes the rest from
+    // TMEM).  Same arithmetic as the L2 variant, so both give the same bits.
     static constexpr int TM_COLS = 512 / (kThreads / 128); // TMEM columns per warp
     static constexpr int TM_SLOTS = TM_COLS / 8;            // chunks of z and r per thread
     static constexpr bool TM_OK = RES_OK && (kThreads % 128) == 0 && TM_SLOTS >= 1;

@@ -1,5 +1,6 @@
 // Kernel parameter block shared by the host driver and the device code.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 namespace gadi {
