@@ -27,6 +27,18 @@ def test_status_strings_and_defaults():
     assert o.tol_h == 1e-3 and o.outer_stag_window == 50
 
 
+def test_resident_defaults():
+    """The resident inner solves are on by default: FP32 takes the
+    tensor-memory H-solve (h_resident 2), BF16 the shared-memory one (1, where
+    tensor memory measured slower), and CGNR on S may run resident."""
+    assert G.default_opts(G.FP32).h_resident == 2
+    assert G.default_opts(G.FP64).h_resident == 2
+    assert G.default_opts(G.BF16).h_resident == 1
+    for prec in (G.FP64, G.FP32, G.BF16):
+        o = G.default_opts(prec)
+        assert o.s_resident == 1 and o.u_r == G.FP64
+
+
 def test_oracle_and_library_share_no_code():
     """The product package and the oracle are independent: neither imports
     the other and they share no source file."""
