@@ -271,12 +271,13 @@ def test_tmem_h_solve_same_bits_as_shared_memory_form(prec, nx, ny, blocks):
 
 @pytest.mark.parametrize("prec", [FP32, BF16])
 @pytest.mark.parametrize("nx,ny,blocks", [(48, 40, 16), (48, 32, 16), (48, 16, 16), (8, 400, 16),
-                                          (2560, 200, 16)])
+                                          (2560, 200, 16), (2560, 120, 16)])
 def test_resident_cgnr_matches_streaming(prec, nx, ny, blocks):
     """CGNR on S with p in shared memory and t, y in tensor memory
     (s_resident = 1, taken with the tensor-memory H-solve when every block
     owns two rows or more; 2560 x 200 FP32 needs more than 16 slots and
-    takes neither) against
+    takes neither, 2560 x 120 FP32 fills all 16 with two column passes)
+    against
     the streaming S-solve (s_resident = 0): both reach 1e-10, outer
     iterations within the precision's band, and the small grids against the
     oracle."""
