@@ -124,7 +124,7 @@ typedef struct {
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
  * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 2
  * (1 for BF16, where tensor memory measured slower), u_r = GADI_FP64,
- * s_resident = 1.  The
+ * s_resident = 1, backward_err = 0.  The
  * step entry gadi_step_solve_h takes the same h_resident default. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
@@ -166,6 +166,13 @@ typedef struct {
                               more (S p is recomputed, never stored); 0 =
                               stream it.  Same arithmetic; the grid-wide
                               sums' order differs.  Other values: INVALID. */
+    int backward_err;      /* gadi_solve: 0 = off; k > 0 = after the solve,
+                              compute the normwise backward error of eq.
+                              (3.2), ||b - A x|| / (||A||_2 ||x|| + ||b||),
+                              into gadi_stats.backward_err, with ||A||_2
+                              from k steps of gadi_norm2_estimate (kept by
+                              the handle for the next solve with the same
+                              k); outside the timed solve.  < 0: INVALID.  */
 } gadi_opts;
 
 typedef struct {
@@ -185,6 +192,10 @@ typedef struct {
     int s_resident;         /* 1 if CGNR on S also ran resident (h_resident
                                = 2 and every block owns >= 2 rows): p in
                                shared memory, t and y in tensor memory       */
+    double backward_err;    /* normwise backward error of eq. (3.2) of the
+                               returned x (gadi_opts.backward_err > 0), with
+                               ||b - A x|| the solve's own final FP64
+                               residual norm; -1 if not computed             */
 } gadi_stats;
 
 typedef struct gadi_handle gadi_handle;
@@ -326,18 +337,24 @@ gadi_status gadi_step_solve_s(gadi_handle *h, double alpha, double omega, gadi_p
  * gadi_solve_h_2d_noalloc: the H-solve of the 2D 5-point class -- CG on
  * (alpha I + M) z = rs with M the h^2-scaled 5-point Laplacian (centre 4,
  * neighbours -1) on an nx x ny grid, from z = 0, with the stopping rules of
- * gadi_step_solve_h -- computed by the same kernel and arithmetic as
- * gadi_step_solve_h, but with no handle and no device allocation.  rs (read)
- * and z (written) are DEVICE u_s vectors of nx*ny elements (double, float or
- * BF16 bits); *its receives the iteration count.
+ * gadi_step_solve_h -- with no handle and no device allocation.  It runs the
+ * streaming form of that H-solve (search direction p in global memory, one
+ * persistent block per SM), which gadi_step_solve_h also takes on grids with
+ * fewer rows than the GPU has SMs; there the two give the same bits.  On
+ * taller grids gadi_step_solve_h keeps p on chip and sums in another order,
+ * so the results then agree to rounding only.  rs (read) and z (written) are
+ * DEVICE u_s vectors of nx*ny elements (double, float or BF16 bits); *its
+ * receives the iteration count.
  *   - Scratch: a file-scope device array of about 10.6 MB that every GPU
  *     loading the library holds until exit; the call makes no cudaMalloc,
  *     cudaFree or other allocating call.
  *   - Limit: nx*ny <= 262144 (for example 512 x 512); larger grids are
  *     rejected with GADI_ERR_INVALID and a message in gadi_last_error().
- *   - The first call on each device looks up the scratch's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The first call on each device (and again after the device's context
+ *     was rebuilt, e.g. by cudaDeviceReset) looks up the scratch's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before any stream capture.
+ *   - Synchronous: the call returns after its GPU work has finished.
  *   - Every call shares the one scratch array and leaves its contents
  *     behind (the call clears what must start at zero).  Calls that overlap
  *     on the GPU -- on different streams or host threads -- race on it and

@@ -810,7 +810,8 @@ int orc_gadi(const orc_problem *p, const double *b, double *x, double alpha, dou
                              : orc_residual(p, prec, b, x, k > 0 ? y : NULL, xn, r, rs);
         memcpy(x, xn, sizeof(double) * m);
         if (k == 0) r0 = rn;
-        double rel = (r0 > 0.0) ? rn / r0 : 0.0;
+        /* r0 = 0: x_0 solves the system; a non-finite r0 gives a NaN relres */
+        double rel = (r0 == 0.0) ? 0.0 : rn / r0;
         if (hist) hist[k] = rel;
         st->relres = rel;
         if (rel <= tol) { status = ORC_OK; break; }

@@ -48,7 +48,8 @@ class Opts(C.Structure):
                 ("inner_stag", C.c_int), ("outer_stag_window", C.c_int),
                 ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
                 ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int),
-                ("h_resident", C.c_int), ("u_r", C.c_int), ("s_resident", C.c_int)]
+                ("h_resident", C.c_int), ("u_r", C.c_int), ("s_resident", C.c_int),
+                ("backward_err", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -56,7 +57,7 @@ class Stats(C.Structure):
                 ("inner_its_s", C.c_longlong), ("relres", C.c_double), ("r0_norm", C.c_double),
                 ("seconds", C.c_double), ("status", C.c_int), ("blocks", C.c_int),
                 ("alpha", C.c_double), ("restarts", C.c_int), ("h_resident", C.c_int),
-                ("s_resident", C.c_int)]
+                ("s_resident", C.c_int), ("backward_err", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -99,6 +99,9 @@ struct gadi_handle {
     double *d_stage = nullptr; // 2 * nelem doubles for host b / x
     double *d_pw = nullptr;    // power-iteration vectors (3 * nelem)
     double *d_sig = nullptr;   // complex class: per-point T (npts), or null
+    double *d_acc = nullptr;   // two doubles: device sums for the backward error
+    double anorm = -1.0;       // ||A||_2 estimate kept for the backward error
+    int anorm_iters = 0;       // power-iteration steps it was taken with
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -594,6 +597,7 @@ gadi_status opts_check(const gadi_opts &o)
     if (o.h_resident < 0 || o.h_resident > 2) return GADI_ERR_INVALID;
     if (o.s_resident != 0 && o.s_resident != 1) return GADI_ERR_INVALID;
     if (o.u_r != GADI_FP64 && o.u_r != GADI_FP64X2) return GADI_ERR_INVALID;
+    if (o.backward_err < 0) return GADI_ERR_INVALID;
     return GADI_OK;
 }
 
@@ -781,7 +785,7 @@ void gadi_destroy(gadi_handle *h)
     if (!h) return;
     void *dev[] = {h->d_rowptr, h->d_col, h->d_mrowptr, h->d_mcol, h->d_aval, h->d_mval, h->d_nval,
                    h->d_atval, h->d_opval, h->d_ws, h->d_part, h->d_hist, h->d_ctl, h->d_bar,
-                   h->d_abort, h->d_flag, h->d_stage, h->d_pw, h->d_sig};
+                   h->d_abort, h->d_flag, h->d_stage, h->d_pw, h->d_sig, h->d_acc};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -879,8 +883,30 @@ gadi_status solve_once(gadi_handle *h, const double *b, double *x, double alpha,
         stats->restarts = 0;
         stats->h_resident = P.resident;
         stats->s_resident = P.s_resident;
+        stats->backward_err = -1.0;
     }
     return (gadi_status)c.status;
+}
+
+// ||v||_2 of an FP64 vector in host or device memory (device: a grid-stride
+// dot on the handle's stream)
+gadi_status vec_norm2(gadi_handle *h, const double *v, long long m, cudaStream_t st, double *out)
+{
+    if (!is_device_ptr(v)) {
+        double s = 0.0;
+        for (long long i = 0; i < m; i++) s = std::fma(v[i], v[i], s);
+        *out = std::sqrt(s);
+        return GADI_OK;
+    }
+    if (!h->d_acc) CK(cudaMalloc(&h->d_acc, 2 * sizeof(double)));
+    CK(cudaMemsetAsync(h->d_acc, 0, sizeof(double), st));
+    k_dot<<<std::max(1, h->nsm * 4), 256, 0, st>>>(v, v, m, h->d_acc);
+    CK(cudaGetLastError());
+    double hs = 0.0;
+    CK(cudaMemcpyAsync(&hs, h->d_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = std::sqrt(hs);
+    return GADI_OK;
 }
 
 // closed-form spectra of the stencil classes (Sec. 4.3, the condition check)
@@ -914,6 +940,29 @@ bool stencil_spectra(const gadi_problem *p, double *lmin, double *lmax, double *
     return true;
 }
 double unit_roundoff(int prec) { return prec == P_BF16 ? 3.91e-3 : (prec == P_FP32 ? 5.96e-8 : 1.11e-16); }
+
+// eq. (3.2): ||r|| / (||A||_2 ||x|| + ||b||) with r_norm the solve's final
+// FP64 residual norm; ||A||_2 from o.backward_err power-iteration steps, kept
+// by the handle for later solves with the same step count
+gadi_status backward_error(gadi_handle *h, const double *b, const double *x, double r_norm, const gadi_opts &o,
+                           double *out)
+{
+    cudaStream_t st = (cudaStream_t)o.stream;
+    if (h->anorm < 0 || h->anorm_iters != o.backward_err) {
+        double an = 0.0;
+        const gadi_status e = gadi_norm2_estimate(h, o.backward_err, &an, o.stream);
+        if (e != GADI_OK) return e;
+        h->anorm = an;
+        h->anorm_iters = o.backward_err;
+    }
+    double xn = 0.0, bn = 0.0;
+    gadi_status e = vec_norm2(h, x, h->nelem, st, &xn);
+    if (e == GADI_OK) e = vec_norm2(h, b, h->nelem, st, &bn);
+    if (e != GADI_OK) return e;
+    const double den = h->anorm * xn + bn;
+    *out = den > 0 ? r_norm / den : 0.0;
+    return GADI_OK;
+}
 } // namespace
 
 extern "C" {
@@ -1002,6 +1051,10 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
     gadi_stats st1;
     gadi_status s = solve_once(h, b, x, alpha, omega, u_high, u_low, tol, maxit, &o, &st1);
     if (s < 0 || o.alpha_restarts <= 0 || (s != GADI_STAGNATED && s != GADI_DIVERGED)) {
+        if (s >= 0 && o.backward_err > 0) {
+            const gadi_status e = backward_error(h, b, x, st1.relres * st1.r0_norm, o, &st1.backward_err);
+            if (e != GADI_OK) return e;
+        }
         if (stats) *stats = st1;
         return s;
     }
@@ -1031,6 +1084,10 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
         acc.status = s;
     }
     acc.relres = rel;
+    if (s >= 0 && o.backward_err > 0) {
+        const gadi_status e = backward_error(h, b, x, rel * r0, o, &acc.backward_err);
+        if (e != GADI_OK) return e;
+    }
     if (stats) *stats = acc;
     return s;
 }
@@ -1177,6 +1234,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.restarts = 0;
             S.h_resident = 0;
             S.s_resident = 0;
+            S.backward_err = -1.0;
         }
     }
     return worst;

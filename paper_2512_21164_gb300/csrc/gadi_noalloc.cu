@@ -35,12 +35,50 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+    unsigned long long ctx_id; // context the address belongs to (0: none yet)
+    void *addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
+
+// Driver entry points for the identity of the current context, resolved once
+// through the runtime (no link against the driver library).  Each context
+// gets a process-unique id, so a context rebuilt after cudaDeviceReset (in
+// which the module, and with it the array, may sit elsewhere) never matches
+// an old entry.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// id of the current context, 0 if it cannot be told (then the address is
+// looked up again on every call)
+unsigned long long current_context_id()
+{
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_current = (CtxGetCurrentFn)f1;
+            g_ctx_id = (CtxGetIdFn)f2;
+        }
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 // Device address of the scratch on the current device.  In host code the
 // symbol names a host-side stand-in, never the device memory, so the address
-// must come from cudaGetSymbolAddress, once per device with that device
-// current.
+// comes from cudaGetSymbolAddress: once per device (and context), with that
+// device current.
 cudaError_t scratch_address(void **out)
 {
     int dev = 0;
@@ -48,13 +86,18 @@ cudaError_t scratch_address(void **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
+    unsigned long long id = current_context_id();
+    if (id != 0 && g_slot[dev].ctx_id == id && g_slot[dev].addr) {
+        *out = g_slot[dev].addr;
+        return cudaSuccess;
     }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch); // creates the context if there is none yet
+    if (e != cudaSuccess) return e;
+    if (id == 0) id = current_context_id();
+    g_slot[dev].ctx_id = id;
+    g_slot[dev].addr = p;
+    *out = p;
     return cudaSuccess;
 }
 

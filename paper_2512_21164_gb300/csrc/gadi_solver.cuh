@@ -576,7 +576,7 @@ struct Runner {
             xb ^= 1;
             const double rn = sqrt(dsum[0]);
             if (k == 0) r0 = rn;
-            rel = r0 > 0.0 ? rn / r0 : 0.0;
+            rel = r0 == 0.0 ? 0.0 : rn / r0; // non-finite r0: NaN, hence DIVERGED
             if (leader) P.hist[k] = rel;
             if (rel <= P.tol) {
                 status = ST_OK;
