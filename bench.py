@@ -55,6 +55,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def traffic_record() -> dict:
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
 def measured_traffic(alg_bytes: float):
     """DRAM bytes of one launch from the committed ncu record (DRAM bytes per
     algorithmic byte of a capped solve of the same kernel, scaled to this
@@ -231,11 +239,29 @@ def run_ours(args):
             torch.cuda.synchronize()
             f_times.append(ev0.elapsed_time(ev1) / 1e3)
         H.apply(G.OP_A, x, r)
-        fp64 = {"seconds": statistics.median(f_times), "status": G.status_str(st64),
+        fp64 = {"seconds": statistics.median(f_times), "step_s": f_times, "status": G.status_str(st64),
                 "outer_its": s64["outer_its"], "inner_its_h": s64["inner_its_h"],
                 "inner_its_s": s64["inner_its_s"],
                 "relres": float(torch.linalg.norm(b - r) / torch.linalg.norm(b)),
                 "kernel_GBps": algorithmic_bytes(n, s64, 8) / s64["seconds"] / 1e9}
+
+    # what binds the mixed kernel: its grid-wide sums (two per CG or CGNR
+    # iteration, one per CGNR set-up and per z/y hand-over) and the FP64
+    # residual step, each measured on its own
+    t_sum = G.probe_sync(0, 20000) * 1e-6
+    y0 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    xo = torch.empty_like(b)
+    rs = torch.empty(n, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        H.step_residual(G.FP32, b, x, y0, xo, None, rs)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(20):
+        H.step_residual(G.FP32, b, x, y0, xo, None, rs)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_res = ev0.elapsed_time(ev1) / 1e3 / 20
+    fp64_gops, fp64_per_clk = G.probe_fp64()
 
     # end-to-end through the C ABI with host (pinned) buffers
     bh = b.cpu().pin_memory()
@@ -254,6 +280,29 @@ def run_ours(args):
     ab = algorithmic_bytes(n, mixed_stats, 4)
     kmean = statistics.mean(kern_s)
     achieved = ab / kmean / 1e9
+    k_out = mixed_stats["outer_its"]
+    n_sums = 2 * (mixed_stats["inner_its_h"] + mixed_stats["inner_its_s"]) + 3 * k_out
+    floor_s = n_sums * t_sum + (k_out + 1) * t_res
+    traffic = measured_traffic(ab)
+    rec = traffic_record()
+    latency = {
+        "grid_sum_us": t_sum * 1e6, "grid_sums": n_sums, "residual_step_ms": t_res * 1e3,
+        "floor_s": floor_s, "kernel_s": kmean, "kernel_over_floor": kmean / floor_s,
+        "note": "floor = grid sums x measured time of one (gadi_probe_sync, 152 blocks) + outer iterations x "
+                "measured FP64 residual step (gadi_step_residual launched alone, launch included); the rest of "
+                "the kernel time is the inner sweeps over vectors held in shared memory, tensor memory and L2"}
+    if fp64 is not None:
+        # GADI-FP64: FP64 pipe operations (an FMA counts one) the method's
+        # definition needs per grid point: residual 8 (x + y, A x in 5,
+        # b - A x, r.r), CG iteration 10 (p update, H p in 5, p.Hp, z, r,
+        # r.r), CGNR iteration 15 (p, S p in 5, u.u, S^T u in 5, y, t, t.t),
+        # CGNR set-up 7 (g, S^T g in 5, t.t)
+        ops = n * (8 * (fp64["outer_its"] + 1) + 10 * fp64["inner_its_h"] + 15 * fp64["inner_its_s"]
+                   + 7 * fp64["outer_its"])
+        fp64["fp64_pipe"] = {"ops": ops, "achieved_gops": ops / fp64["seconds"] / 1e9,
+                             "peak_gops": fp64_gops, "frac": ops / fp64["seconds"] / 1e9 / fp64_gops,
+                             "peak_fma_per_sm_clk": fp64_per_clk,
+                             "peak_source": "measured (gadi_probe_fp64: 8 independent FMA chains per thread)"}
     out = {
         "metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
         "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -269,7 +318,10 @@ def run_ours(args):
         "fp64_plain": fp64,
         "speedup_vs_fp64": (fp64["seconds"] / value) if fp64 else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": measured_traffic(ab), "peak_source": src,
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                     "dram_gbs": traffic / kmean / 1e9 if traffic else None,
+                     "l2_throughput_pct": rec.get("l2_throughput_pct") if traffic else None,
+                     "latency": latency,
                      "kernel": "gadi_stencil_kernel<2D5,FP32> (persistent, one launch per solve; H-solve: "
                                + H_SOLVE[mixed_stats["h_resident"]] + "; S-solve: "
                                + ("p in shared memory, t and y in tensor memory" if mixed_stats.get("s_resident")
@@ -283,7 +335,7 @@ def run_ours(args):
         "step_s": per,
     }
     if rank == 0 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(p, xt, alpha, mixed_stats, args.cpu_outer)
+        out["cpu_baseline"] = cpu_baseline()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -334,7 +386,9 @@ def record_traffic(rep: str, case_log: str):
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
     got = {}
     for k, u, v in zip(head, units, vals):
-        if k in ("dram__bytes_read.sum", "dram__bytes_write.sum", "Kernel Name", "gpu__time_duration.sum"):
+        if k in ("dram__bytes_read.sum", "dram__bytes_write.sum", "Kernel Name", "gpu__time_duration.sum",
+                 "lts__throughput.avg.pct_of_peak_sustained_elapsed",
+                 "gpu__compute_memory_throughput.avg.pct_of_peak_sustained_elapsed"):
             got[k] = (v, u)
     dram = sum(float(got[k][0].replace(",", "")) * scale[got[k][1]]
                for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
@@ -346,6 +400,8 @@ def record_traffic(rep: str, case_log: str):
            "outer_its": stats["outer_its"], "inner_its_h": stats["inner_its_h"],
            "inner_its_s": stats["inner_its_s"], "dram_bytes": dram, "algorithmic_bytes": alg,
            "dram_bytes_per_algorithmic_byte": dram / alg, "kernel_source_hash": kernel_source_hash(),
+           "l2_throughput_pct": float(got["lts__throughput.avg.pct_of_peak_sustained_elapsed"][0].replace(",", ""))
+           if "lts__throughput.avg.pct_of_peak_sustained_elapsed" in got else None,
            "source": f"ncu -i {os.path.basename(rep)} (dram__bytes_read.sum + dram__bytes_write.sum)"}
     with open(TRAFFIC_RECORD, "w") as f:
         json.dump(rec, f, indent=1)
@@ -589,50 +645,95 @@ def run_batched(args):
             H.close()
 
 
-def cpu_baseline(p, xt, alpha, gpu_stats, outer):
-    """The CPU oracle timed on a bounded sample: `outer` outer iterations of
-    Algorithm 1 (FP64 outer, FP32 inner) on the full grid, scaled to the
-    number of outer iterations the mixed solve needed."""
+TWIN = 256  # the CPU oracle's twin of the 2048^2 workload (same beta draw, alpha/alpha*, omega, tolerances)
+
+
+def _twin():
+    from workloads import SEED_C2, alpha_star, conv_diff_2d
+    p, xt = conv_diff_2d(TWIN, SEED_C2)
+    return p, xt, ALPHA_FACTOR * alpha_star(p)
+
+
+def _twin_desc():
+    return (f"conv-diff-2d {TWIN}x{TWIN} twin of the {WORKLOAD} workload (same beta draw, alpha = "
+            f"{ALPHA_FACTOR:g} alpha* of the twin, omega = {OMEGA:g}, tol_h = tol_s = {TOL_H:g}, FP32 inner), "
+            f"solved to 1e-10 by the C oracle")
+
+
+def _oracle_solve(omp, p, xt, alpha):
+    """One oracle solve of Algorithm 1 to 1e-10 (FP64 outer, FP32 inner);
+    returns (seconds, stats)."""
     import oracle as O
-    orc = O.Oracle(p)
+    orc = O.Oracle(p, omp=omp)
     b = orc.rhs(xt)
     t0 = time.perf_counter()
-    _, st = orc.gadi(b, alpha, OMEGA, O.FP32, tol=0.0, maxit=outer, tol_h=TOL_H, tol_s=TOL_S,
-                     outer_stag_window=0)
-    dt = time.perf_counter() - t0
-    per_outer = dt / max(1, st["outer_its"])
-    k = gpu_stats["outer_its"]
-    return {"value": per_outer * k, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"{st['outer_its']} outer iterations of the C oracle (single thread) on the full "
-                      f"2048^2 grid in {dt:.1f} s, scaled by the {k} outer iterations of the mixed solve"}
+    _, st = orc.gadi(b, alpha, OMEGA, O.FP32, tol=TOL, maxit=MAXIT, tol_h=TOL_H, tol_s=TOL_S)
+    return time.perf_counter() - t0, st
+
+
+def _omp_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+
+
+def cpu_baseline():
+    """The CPU oracle timed to tolerance on this host (no extrapolation):
+    the 256^2 twin of the workload single-threaded (the oracle as it stands,
+    the reported value) and in the all-core OpenMP build, and config 1
+    (64^2, plain FP64, alpha 0.5, omega 1, 500-iteration cap) at full size."""
+    import oracle as O
+    from workloads import config1
+    p, xt, alpha = _twin()
+    t1, st1 = _oracle_solve(False, p, xt, alpha)
+    out = {"value": t1, "unit": "s", "cores": 1, "kind": "oracle",
+           "sample": _twin_desc() + f", single thread: {st1['status']} after {st1['outer_its']} outer / "
+                     f"{st1['inner_h']} H / {st1['inner_s']} S iterations, relres {st1['relres']:.3g}",
+           "host_cpus": os.cpu_count()}
+    if O.has_openmp():
+        tm, stm = _oracle_solve(True, p, xt, alpha)
+        out["openmp"] = {"value": tm, "unit": "s", "cores": _omp_threads(), "status": stm["status"],
+                         "outer_its": stm["outer_its"]}
+    else:
+        out["openmp"] = {"unavailable": "gcc without OpenMP on this host"}
+    p1, xt1, c = config1()
+    orc = O.Oracle(p1)
+    b1 = orc.rhs(xt1)
+    t0 = time.perf_counter()
+    _, s1 = orc.gadi(b1, c["alpha"], c["omega"], O.FP64, tol=c["tol"], maxit=c["maxit"])
+    out["config1"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": 1, "status": s1["status"],
+                      "outer_its": s1["outer_its"], "relres": s1["relres"],
+                      "workload": "conv-diff-2d 64x64, beta=(10,10), alpha=0.5, omega=1, maxit 500, plain FP64"}
+    return out
 
 
 def run_reference(args):
+    """The CPU oracle (all-core OpenMP build where gcc has OpenMP, else the
+    single-threaded one) solving the 256^2 twin of the workload to 1e-10,
+    once per step: a real bounded run, timed on the host cores, rank 0 only."""
+    import oracle as O
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from workloads import alpha_star, config2
-    p, xt = config2(args.grid)
-    alpha = ALPHA_FACTOR * alpha_star(p)
-    # scaled to the outer iterations the mixed solve needs on this workload
-    # (2585, measured on GB300); the arm times the oracle's cost per outer
-    # iteration on a bounded sample, not a full oracle solve
-    counts = {"outer_its": args.ref_outer}
-    vals = []
-    cb = None
+    omp = O.has_openmp()
+    p, xt, alpha = _twin()
+    vals, st = [], None
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(p, xt, alpha, counts, 1)
+        dt, st = _oracle_solve(omp, p, xt, alpha)
         if i >= args.warmup:
-            vals.append(cb["value"])
+            vals.append(dt)
     v = statistics.mean(vals)
-    cb["value"] = v
+    cores = _omp_threads() if omp else 1
+    cb = {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+          "sample": _twin_desc() + f" ({'OpenMP, all host cores' if omp else 'single thread'}): "
+                    f"{st['status']} after {st['outer_its']} outer iterations, relres {st['relres']:.3g}"}
     out = {"metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
            "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64 outer / f32 inner", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "alpha_over_alpha_star": ALPHA_FACTOR, "omega": OMEGA},
-           "cpu_baseline": cb,
+           "config": {"workload": f"conv-diff-2d {TWIN}x{TWIN} (twin of the 2048x2048 workload)",
+                      "twin_of": WORKLOAD, "alpha_over_alpha_star": ALPHA_FACTOR, "omega": OMEGA,
+                      "tol_h": TOL_H, "tol_s": TOL_S, "u_s": "fp32", "u": "fp64"},
+           "step_s": vals, "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -645,11 +746,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=2048)
     ap.add_argument("--maxit", type=int, default=MAXIT)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-outer", type=int, default=1)
-    ap.add_argument("--ref-outer", type=int, default=2585)
     ap.add_argument("--profile-case", choices=["fp64", "fp32", "bf16"], default=None,
                     help="run one solve capped at --maxit outer iterations (for ncu) and exit")
     ap.add_argument("--grids", default=None, help="paper2d / paper3d / paperc: comma-separated grid sizes")

@@ -276,6 +276,27 @@ gadi_status gadi_select_alpha(const gadi_problem *prob, double alpha0, gadi_prec
  * not in (0, 10000]), CUDA. */
 gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms);
 
+/* Timing probe of the grid-wide sum (no counterpart in the paper): runs
+ * `iters` grid-wide sums of two FP32 partials per thread on `nblocks`
+ * persistent blocks of the solve kernels' size (0 = one per SM), each taken
+ * exactly as the inner solves take theirs (block tree, one partial per block,
+ * the bounded grid barrier, every block reading all partials), and returns
+ * the mean time of one sum in microseconds (device %globaltimer).  CG on H
+ * and CGNR on S each take two such sums per iteration, so this is their
+ * latency floor.  Synchronous on the legacy default stream.  Errors: INVALID
+ * (iters not in [1, 1e6], nblocks above the co-resident maximum), TIMEOUT,
+ * CUDA. */
+gadi_status gadi_probe_sync(int nblocks, int iters, double *us_per_sum);
+
+/* Timing probe of the FP64 pipe (no counterpart in the paper): one block of
+ * the solve kernels' size per SM runs `iters` rounds of 8 independent FP64
+ * fused multiply-adds per thread; *gops receives the rate in 10^9 FMA per
+ * second (CUDA events), *sm_ops_per_clk (nullable) the same per SM and
+ * clock at the device's nominal SM clock.  The rate bounds every FP64 step
+ * of the method (the residual, GADI-FP64's inner solves).  Synchronous on
+ * the legacy default stream.  Errors: INVALID (iters not in [1, 1e7]), CUDA. */
+gadi_status gadi_probe_fp64(int iters, double *gops, double *sm_ops_per_clk);
+
 /* Check of the library's integer-pipe number conversions (no counterpart in
  * the paper): for each of the n doubles at `in` (DEVICE pointer, n >= 0),
  * compares on the device (1) binary64 -> binary32 round-to-nearest-even,

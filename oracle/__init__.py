@@ -29,24 +29,47 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gadi_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+# the same source built with -fopenmp: the all-core CPU baseline only (its
+# sums are split by thread); parity tests use the sequential build above
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 FP64, FP32, BF16 = 0, 1, 2
 K_2D5, K_3D7, K_C2D5, K_CSR = 0, 1, 2, 3
 OP_A, OP_M, OP_N = 0, 1, 2
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "STAGNATED", 3: "DIVERGED"}
+_FLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def _compile(out, extra):
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *_FLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/_build/liboracle.so (gcc, no FMA)."""
+    """Compile the C oracle into oracle/_build/liboracle.so (gcc, no FMA
+    contraction, no OpenMP) and, where gcc has OpenMP, the all-core variant
+    liboracle_omp.so used only to time the CPU baseline."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    if force:
+        for f in (_LIB, _LIB_OMP):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(_LIB, [])
+    try:
+        _compile(_LIB_OMP, ["-fopenmp"])
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP here: the all-core baseline is reported as unavailable
     return _LIB
+
+
+def has_openmp() -> bool:
+    build()
+    return os.path.exists(_LIB_OMP)
 
 
 class _Problem(C.Structure):
@@ -71,11 +94,15 @@ class _Stats(C.Structure):
                 ("relres", C.c_double), ("status", C.c_int)]
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The loaded oracle library; omp=True: the all-core (OpenMP) build."""
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if omp not in _libs:
+            build()
+            path = _LIB_OMP if omp else _LIB
+            if not os.path.exists(path):
+                raise RuntimeError("the OpenMP build of the oracle is unavailable (gcc without -fopenmp)")
+            L = C.CDLL(path)
             dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
             pp = C.POINTER(_Problem)
             L.orc_round_bf16.restype = C.c_double
@@ -102,8 +129,8 @@ def lib():
             L.orc_gadi.restype = C.c_int
             L.orc_gadi.argtypes = [pp, dp, dp, C.c_double, C.c_double, C.c_int, C.c_double,
                                    C.c_int, C.POINTER(_Opts), C.POINTER(_Stats), dp]
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
 
 
 def _dp(a):
@@ -144,8 +171,9 @@ def csr_split(rowptr, col, val):
 class Oracle:
     """Bound oracle for one problem (workloads.Problem)."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, omp: bool = False):
         self.prob = prob
+        self.L = lib(omp)
         self._keep = []
         P = _Problem()
         P.kind, P.nx, P.ny, P.nz = prob.kind, prob.nx, prob.ny, prob.nz
@@ -176,7 +204,7 @@ class Oracle:
     def apply(self, which, x):
         x = _f64(x)
         y = np.empty(self.m)
-        lib().orc_apply(C.byref(self.P), which, _dp(x), _dp(y))
+        self.L.orc_apply(C.byref(self.P), which, _dp(x), _dp(y))
         return y
 
     def rhs(self, x_true):
@@ -186,7 +214,7 @@ class Oracle:
     def coeffs(self, part):
         out = np.zeros(8)
         b = (C.c_double * 3)(*self.prob.beta)
-        lib().orc_stencil_coeffs(self.prob.kind, part, self.prob.hh, b, self.prob.kappa,
+        self.L.orc_stencil_coeffs(self.prob.kind, part, self.prob.hh, b, self.prob.kappa,
                                  self.prob.sigma, _dp(out))
         return out
 
@@ -196,7 +224,7 @@ class Oracle:
         b, x = _f64(b), _f64(x)
         yy = _f64(y) if y is not None else None
         xo, r, rs = np.empty(self.m), np.empty(self.m), np.empty(self.m)
-        nrm = lib().orc_residual(C.byref(self.P), prec, _dp(b), _dp(x),
+        nrm = self.L.orc_residual(C.byref(self.P), prec, _dp(b), _dp(x),
                                  _dp(yy) if yy is not None else None, _dp(xo), _dp(r), _dp(rs))
         return xo, r, rs, nrm
 
@@ -206,7 +234,7 @@ class Oracle:
         b, x = _f64(b), _f64(x)
         yy = _f64(y) if y is not None else None
         xo, rh, rl, rs = (np.empty(self.m) for _ in range(4))
-        nrm = lib().orc_residual_dd(C.byref(self.P), prec, _dp(b), _dp(x),
+        nrm = self.L.orc_residual_dd(C.byref(self.P), prec, _dp(b), _dp(x),
                                     _dp(yy) if yy is not None else None, _dp(xo), _dp(rh), _dp(rl),
                                     _dp(rs))
         return xo, rh, rl, rs, nrm
@@ -214,13 +242,13 @@ class Oracle:
     def solve_h(self, alpha, prec, rs, tol, maxit=1000, stag=10):
         rs = _f64(rs)
         z = np.empty(self.m)
-        its = lib().orc_solve_h(C.byref(self.P), alpha, prec, _dp(rs), _dp(z), tol, maxit, stag)
+        its = self.L.orc_solve_h(C.byref(self.P), alpha, prec, _dp(rs), _dp(z), tol, maxit, stag)
         return z, its
 
     def solve_s(self, alpha, omega, prec, z, tol, maxit=1000, stag=10, pointwise=False):
         z = _f64(z)
         y = np.empty(self.m)
-        its = lib().orc_solve_s(C.byref(self.P), alpha, omega, prec, _dp(z), _dp(y), tol, maxit,
+        its = self.L.orc_solve_s(C.byref(self.P), alpha, omega, prec, _dp(z), _dp(y), tol, maxit,
                                 stag, int(pointwise))
         return y, its
 
@@ -235,7 +263,7 @@ class Oracle:
                   int(residual_dd))
         st = _Stats()
         hist = np.zeros(maxit + 2)
-        lib().orc_gadi(C.byref(self.P), _dp(b), _dp(x), alpha, omega, prec, tol, maxit,
+        self.L.orc_gadi(C.byref(self.P), _dp(b), _dp(x), alpha, omega, prec, tol, maxit,
                        C.byref(o), C.byref(st), _dp(hist))
         k = st.outer_its
         return x, dict(outer_its=k, inner_h=st.inner_h, inner_s=st.inner_s, relres=st.relres,

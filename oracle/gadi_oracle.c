@@ -46,6 +46,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Parallel loops for the all-core build of the timed CPU baseline (built with
+ * -fopenmp into a second library).  The default build, the one every parity
+ * test uses, is compiled without OpenMP: these expand to nothing and every
+ * loop and sum runs sequentially in index order.  In the OpenMP build the
+ * sums are split by thread, which changes only their rounding order. */
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define OMP_FOR ORC_PRAGMA(omp parallel for schedule(static))
+#define OMP_FOR_COLLAPSE2 ORC_PRAGMA(omp parallel for collapse(2) schedule(static))
+#define OMP_FOR_SUM(v) ORC_PRAGMA(omp parallel for reduction(+ : v) schedule(static))
+#else
+#define OMP_FOR
+#define OMP_FOR_COLLAPSE2
+#define OMP_FOR_SUM(v)
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* precisions (u_s)                                                          */
 /* ------------------------------------------------------------------------ */
@@ -177,6 +193,7 @@ static long nbr(const orc_op *op, int ix, int iy, int iz, int dir)
 static void apply_d(const orc_op *op, const double *x, double *y)
 {
     if (op->kind == ORC_K_CSR) {
+        OMP_FOR
         for (int i = 0; i < op->n; i++) {
             double s = op->d * x[i];
             for (int k = op->rowptr[i]; k < op->rowptr[i + 1]; k++)
@@ -188,6 +205,7 @@ static void apply_d(const orc_op *op, const double *x, double *y)
     int nz = op->kind == ORC_K_3D7 ? op->nz : 1;
     int ndir = op->kind == ORC_K_3D7 ? 6 : 4;
     int cplx = op->kind == ORC_K_C2D5;
+    OMP_FOR_COLLAPSE2
     for (int iz = 0; iz < nz; iz++)
         for (int iy = 0; iy < op->ny; iy++)
             for (int ix = 0; ix < op->nx; ix++) {
@@ -229,6 +247,7 @@ typedef struct {
 static void apply_f(const orc_op *op, const op_f *cf, const float *x, float *y)
 {
     if (op->kind == ORC_K_CSR) {
+        OMP_FOR
         for (int i = 0; i < op->n; i++) {
             float s = cf->d * x[i];
             for (int k = op->rowptr[i]; k < op->rowptr[i + 1]; k++)
@@ -240,6 +259,7 @@ static void apply_f(const orc_op *op, const op_f *cf, const float *x, float *y)
     int nz = op->kind == ORC_K_3D7 ? op->nz : 1;
     int ndir = op->kind == ORC_K_3D7 ? 6 : 4;
     int cplx = op->kind == ORC_K_C2D5;
+    OMP_FOR_COLLAPSE2
     for (int iz = 0; iz < nz; iz++)
         for (int iy = 0; iy < op->ny; iy++)
             for (int ix = 0; ix < op->nx; ix++) {
@@ -453,6 +473,7 @@ static void free_ops(gadi_ops *g)
 static double dot_d(int m, const double *a, const double *b)
 {
     double s = 0.0;
+    OMP_FOR_SUM(s)
     for (int i = 0; i < m; i++) s = s + a[i] * b[i];
     return s;
 }
@@ -463,6 +484,7 @@ static double dot_d(int m, const double *a, const double *b)
 static float dot_f(int m, const float *a, const float *b)
 {
     double s = 0.0;
+    OMP_FOR_SUM(s)
     for (int i = 0; i < m; i++) s = s + (double)a[i] * (double)b[i];
     return (float)s;
 }
@@ -479,6 +501,7 @@ static int cg_d(const orc_op *op1, const orc_op *op2, const double *rhs, double 
     for (int i = 0; i < m; i++) xsol[i] = 0.0;
     if (rr0 == 0.0) return 0;
     for (int j = 0; j < maxit; j++) {
+        OMP_FOR
         for (int i = 0; i < m; i++) p[i] = (j == 0) ? r[i] : fma(beta, p[i], r[i]);
         double pq;
         if (op2 == NULL) {
@@ -490,6 +513,7 @@ static int cg_d(const orc_op *op1, const orc_op *op2, const double *rhs, double 
             apply_d(op2, u, q);          /* q = S^T u        */
         }
         double a = rr / pq;
+        OMP_FOR
         for (int i = 0; i < m; i++) {
             xsol[i] = (j == 0) ? a * p[i] : fma(a, p[i], xsol[i]);
             r[i] = fma(-a, q[i], r[i]);
@@ -517,6 +541,7 @@ static int cg_f(const orc_op *op1, const op_f *f1, const orc_op *op2, const op_f
     for (int i = 0; i < m; i++) xsol[i] = 0.0f;
     if (rr0 == 0.0f) return 0;
     for (int j = 0; j < maxit; j++) {
+        OMP_FOR
         for (int i = 0; i < m; i++) p[i] = st_f(prec, (j == 0) ? r[i] : r[i] + beta * p[i]);
         float pq;
         if (op2 == NULL) {
@@ -524,11 +549,13 @@ static int cg_f(const orc_op *op1, const op_f *f1, const orc_op *op2, const op_f
             pq = dot_f(m, p, q);
         } else {
             apply_f(op1, f1, p, u);            /* u = S p, stored: rounded to u_s */
+            OMP_FOR
             for (int i = 0; i < m; i++) u[i] = st_f(prec, u[i]);
             pq = dot_f(m, u, u);
             apply_f(op2, f2, u, q);
         }
         float a = rr / pq;
+        OMP_FOR
         for (int i = 0; i < m; i++) {
             xsol[i] = st_f(prec, (j == 0) ? a * p[i] : xsol[i] + a * p[i]);
             r[i] = st_f(prec, r[i] - a * q[i]);
@@ -561,8 +588,10 @@ int orc_solve_h(const orc_problem *p, double alpha, int prec, const double *rs, 
     } else {
         float *w = (float *)malloc(sizeof(float) * 6 * (size_t)(m > 0 ? m : 1));
         float *rf = w + 4 * m, *zf = w + 5 * m;
+        OMP_FOR
         for (int i = 0; i < m; i++) rf[i] = (float)rs[i];
         its = cg_f(&g.H, &g.Hf, NULL, NULL, prec, rf, zf, tol, maxit, stag, w);
+        OMP_FOR
         for (int i = 0; i < m; i++) z[i] = (double)zf[i];
         free(w);
     }
@@ -633,9 +662,11 @@ double orc_residual(const orc_problem *p, int prec, const double *b, const doubl
     if (build_ops(p, 1.0, prec, &g)) return -1.0;
     int m = op_len(&g.A);
     double *ax = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    OMP_FOR
     for (int i = 0; i < m; i++) x_out[i] = y ? x[i] + y[i] : x[i];
     apply_d(&g.A, x_out, ax);
     double s = 0.0;
+    OMP_FOR_SUM(s)
     for (int i = 0; i < m; i++) {
         r[i] = b[i] - ax[i];
         s = s + r[i] * r[i];

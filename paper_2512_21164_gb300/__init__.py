@@ -107,6 +107,10 @@ def lib():
             L.gadi_select_alpha.restype = C.c_int
             L.gadi_selftest_barrier.argtypes = [C.c_int, C.c_double]
             L.gadi_selftest_barrier.restype = C.c_int
+            L.gadi_probe_sync.argtypes = [C.c_int, C.c_int, dp]
+            L.gadi_probe_sync.restype = C.c_int
+            L.gadi_probe_fp64.argtypes = [C.c_int, dp, dp]
+            L.gadi_probe_fp64.restype = C.c_int
             L.gadi_selftest_convert.argtypes = [vp, C.c_longlong, C.POINTER(C.c_longlong)]
             L.gadi_selftest_convert.restype = C.c_int
             L.gadi_solve_h_2d_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, vp, vp,
@@ -291,6 +295,25 @@ def selftest_barrier(nblocks=64, timeout_ms=50.0):
     """gadi_selftest_barrier: a grid barrier whose wait runs out; returns the status
     (GADI_ERR_TIMEOUT expected)."""
     return lib().gadi_selftest_barrier(int(nblocks), float(timeout_ms))
+
+
+def probe_sync(nblocks=0, iters=20000):
+    """gadi_probe_sync: mean microseconds of one grid-wide sum of the inner
+    solves (two FP32 values, bounded grid barrier) on `nblocks` blocks."""
+    out = C.c_double()
+    st = lib().gadi_probe_sync(int(nblocks), int(iters), C.byref(out))
+    if st != OK:
+        raise GadiError(st, "gadi_probe_sync")
+    return out.value
+
+
+def probe_fp64(iters=200000):
+    """gadi_probe_fp64: (10^9 FP64 FMA per second, FMA per SM per clock)."""
+    g, r = C.c_double(), C.c_double()
+    st = lib().gadi_probe_fp64(int(iters), C.byref(g), C.byref(r))
+    if st != OK:
+        raise GadiError(st, "gadi_probe_fp64")
+    return g.value, r.value
 
 
 def selftest_convert(d):

@@ -509,6 +509,56 @@ __global__ void k_barrier_selftest(unsigned long long *counter, int *abort_flag,
     (void)gs.sync();
 }
 
+// `iters` grid-wide sums of two FP32 partials, each exactly as the inner
+// solves take one (block tree, partial to a slot, grid barrier, every block
+// loads all partials); block 0 reports the elapsed %globaltimer time.  The
+// partials stay finite (each round feeds a scaled total back in).
+__global__ void __launch_bounds__(kThreadsHost, 1)
+    k_probe_sync(double *part, unsigned long long *counter, int *abort_flag, int iters, unsigned long long *t_out,
+                 float *sink)
+{
+    GridSync gs;
+    gs.counter = counter;
+    gs.abort_flag = abort_flag;
+    gs.nblocks = gridDim.x;
+    const int G = gridDim.x;
+    float acc[2] = {(float)threadIdx.x * 1e-3f, 1.0f}, out[2] = {0.f, 0.f};
+    int slot = 0;
+    if (!gs.sync()) return;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 0; i < iters; i++) {
+        float *pt = reinterpret_cast<float *>(part + (size_t)slot * 2 * G);
+        block_partials_write<2, float>(acc, pt, G, blockIdx.x);
+        if (!gs.sync()) return;
+        grid_partials_sum<2, float>(pt, G, out);
+        acc[0] = out[0] * 1e-6f + (float)threadIdx.x * 1e-3f;
+        slot ^= 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *t_out = globaltimer_ns() - t0;
+        *sink = out[0] + out[1];
+    }
+}
+
+// FP64 fused multiply-add throughput: 8 independent chains per thread (the
+// pipe, not the chain latency, sets the rate), `iters` rounds; the results
+// are stored so the chains are not removed
+__global__ void __launch_bounds__(kThreadsHost, 1) k_probe_dfma(int iters, double *sink)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = 1.0 + 1e-9 * (threadIdx.x + k);
+    const double m = 0.999999999, c = 1e-12 * (blockIdx.x + 1);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = fma(a[k], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) t += a[k];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 gadi_status check_finite_dev(gadi_handle *h, const double *v, long long n, cudaStream_t st, bool *ok)
 {
     CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), st));
@@ -1009,6 +1059,80 @@ gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms)
     if (e != cudaSuccess) st = cuda_err(e, "gadi_selftest_barrier", __LINE__);
     else if (hab) st = GADI_ERR_TIMEOUT;
     cudaFree(buf);
+    return st;
+}
+
+gadi_status gadi_probe_sync(int nblocks, int iters, double *us_per_sum)
+{
+    if (!us_per_sum || iters <= 0 || iters > 1000000) return GADI_ERR_INVALID;
+    int dev = 0, nsm = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_probe_sync, kThreadsHost, 0));
+    if (nblocks == 0) nblocks = nsm;
+    if (nblocks < 1 || nblocks > per_sm * nsm) return GADI_ERR_INVALID;
+    // partials (2 slots x 2 values x nblocks doubles), counter, abort flag,
+    // elapsed time, sink
+    const size_t part_bytes = sizeof(double) * 4 * (size_t)nblocks;
+    char *buf = nullptr;
+    CK(cudaMalloc(&buf, part_bytes + 256));
+    double *part = (double *)buf;
+    unsigned long long *counter = (unsigned long long *)(buf + part_bytes);
+    int *abort_flag = (int *)(buf + part_bytes + 64);
+    unsigned long long *t_out = (unsigned long long *)(buf + part_bytes + 128);
+    float *sink = (float *)(buf + part_bytes + 192);
+    void *args[] = {&part, &counter, &abort_flag, &iters, &t_out, &sink};
+    unsigned long long tns = 0;
+    int hab = 0;
+    gadi_status st = GADI_OK;
+    cudaError_t e = cudaMemset(buf, 0, part_bytes + 256);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((const void *)k_probe_sync, dim3(nblocks), dim3(kThreadsHost), args, 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&tns, t_out, sizeof tns, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hab, abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = cuda_err(e, "gadi_probe_sync", __LINE__);
+    else if (hab) st = GADI_ERR_TIMEOUT;
+    else *us_per_sum = (double)tns * 1e-3 / iters;
+    cudaFree(buf);
+    return st;
+}
+
+gadi_status gadi_probe_fp64(int iters, double *gops, double *sm_ops_per_clk)
+{
+    if (!gops || iters <= 0 || iters > 10000000) return GADI_ERR_INVALID;
+    int dev = 0, nsm = 0, clk_khz = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev));
+    double *sink = nullptr;
+    CK(cudaMalloc(&sink, sizeof(double) * (size_t)nsm * kThreadsHost));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gadi_status st = GADI_OK;
+    float ms = 0.f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        k_probe_dfma<<<nsm, kThreadsHost>>>(iters / 10 + 1, sink); // warm-up (clocks, code)
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) {
+        k_probe_dfma<<<nsm, kThreadsHost>>>(iters, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) st = cuda_err(e, "gadi_probe_fp64", __LINE__);
+    else {
+        const double ops = 8.0 * iters * (double)nsm * kThreadsHost;
+        *gops = ops / (ms * 1e-3) / 1e9;
+        if (sm_ops_per_clk) *sm_ops_per_clk = ops / (ms * 1e-3) / nsm / (clk_khz * 1e3);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
     return st;
 }
 

@@ -400,3 +400,81 @@ def test_paper_complex_instance_matches_oracle(prec):
     assert so["status"] == "OK" and st == G.OK, G.status_str(st)
     assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"])
     assert np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b) <= 1e-10
+
+
+def test_headline_geometry_solve_matches_oracle():
+    """The 2048^2 benchmark's kernel configuration on a grid the oracle
+    solves in about a minute: FP32 inner, omega = 0, inner tolerances 1e-3,
+    2048 x 224 on 16 blocks -- 14 rows per block and one column pass, as each
+    of the benchmark's 152 blocks has on 2048^2 -- so the H-solve keeps p in
+    shared memory and z, r in tensor memory (14 of 16 slots) and CGNR on S
+    runs resident.  alpha = 2 alpha* of this grid (about 1200 outer
+    iterations; 8 alpha* needs about 4500 on this narrower grid).  The
+    oracle runs in its all-core build (the same arithmetic, its sums split by
+    thread).  Against it: outer iterations within +-10 %, relres and backward
+    error <= 1e-10, forward error within 10x, and the opt-in backward error
+    of gadi_stats."""
+    p, xt = conv_diff_2d(2048, 2, ny=224)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    alpha = 2 * alpha_star(p)
+    omp = O.Oracle(p, omp=True) if O.has_openmp() else orc
+    xo, so = omp.gadi(b, alpha, 0.0, FP32, tol=1e-10, maxit=20000, tol_h=1e-3, tol_s=1e-3)
+    st, sg, xg, hg = _gpu_solve(p, b, alpha, 0.0, FP32, 1e-10, 20000, max_blocks=16, backward_err=50)
+    assert so["status"] == "OK" and st == G.OK, (so["status"], G.status_str(st))
+    assert (sg["blocks"], sg["h_resident"], sg["s_resident"]) == (16, 2, 1), sg
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, 0.10 * so["outer_its"]), \
+        (sg["outer_its"], so["outer_its"])
+    r = b - orc.apply(O.OP_A, xg)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1e-10 and abs(rel - sg["relres"]) <= 1e-3 * rel
+    Anorm = O.norm2_power(lambda v: orc.apply(O.OP_A, v),
+                          lambda v: orc.apply(O.OP_M, v) - orc.apply(O.OP_N, v), p.nvec, iters=50)
+    be = O.backward_error(np.linalg.norm(r), Anorm, xg, b)
+    assert be <= 1e-10
+    assert abs(sg["backward_err"] - be) <= 1e-2 * be, (sg["backward_err"], be)
+    fe_g = np.linalg.norm(xg - xt) / np.linalg.norm(xt)
+    fe_o = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+    assert fe_g <= 10 * fe_o + 1e-14, (fe_g, fe_o)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+def test_backward_err_stat_matches_oracle(prec):
+    """gadi_stats.backward_err (opt-in) is eq. (3.2) of the returned x, host
+    and device vectors alike; off by default (-1)."""
+    import torch
+    p, xt = conv_diff_2d(40, 211, ny=36)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    a = 2 * alpha_star(p)
+    with G.Gadi.from_problem(p) as H:
+        xd = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+        st, s = H.solve(dev64(b), xd, a, 1.0, prec, 1e-8, 2000, backward_err=100)
+        xh = np.zeros(p.nvec)
+        st2, s2 = H.solve(b, xh, a, 1.0, prec, 1e-8, 2000, backward_err=100)
+        _, s3 = H.solve(b, np.zeros(p.nvec), a, 1.0, prec, 1e-8, 2000)
+    assert st == st2 == G.OK and s3["backward_err"] == -1.0
+    xg = xd.cpu().numpy()
+    A = orc.dense(O.OP_A) if p.nvec <= 400 else None
+    Anorm = np.linalg.norm(A, 2) if A is not None else O.norm2_power(
+        lambda v: orc.apply(O.OP_A, v), lambda v: orc.apply(O.OP_M, v) - orc.apply(O.OP_N, v), p.nvec, 200)
+    be = O.backward_error(np.linalg.norm(b - orc.apply(O.OP_A, xg)), Anorm, xg, b)
+    assert abs(s["backward_err"] - be) <= 1e-3 * be, (s["backward_err"], be)
+    assert abs(s2["backward_err"] - s["backward_err"]) <= 1e-12 * be
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_diverged_rule_matches_oracle(prec):
+    """A = -(1 + 1/4) I (CSR): relres_k = 9^k exactly in closed form, so both
+    sides must report DIVERGED at the first k with relres > 1e6 (k = 7)."""
+    from workloads import K_CSR, Problem
+    n = 4
+    p = Problem(K_CSR, n, rowptr=np.arange(n + 1, dtype=np.int32), col=np.arange(n, dtype=np.int32),
+                val=np.full(n, -1.25))
+    orc = O.Oracle(p)
+    b = np.array([1.0, -2.0, 0.5, 3.0])
+    _, so = orc.gadi(b, 1.0, 0.0, prec, tol=1e-10, maxit=50, outer_stag_window=0)
+    st, sg, xg, hg = _gpu_solve(p, b, 1.0, 0.0, prec, 1e-10, 50, outer_stag_window=0)
+    assert so["status"] == "DIVERGED" and st == G.DIVERGED
+    assert sg["outer_its"] == so["outer_its"] == 7
+    assert np.allclose(hg, 9.0 ** np.arange(8), rtol=1e-9)
