@@ -560,7 +560,8 @@ def run_workload(args):
         alpha, omega, maxit = c["alpha"], c["omega"], c["maxit"]
     elif name == "c3":
         p, xt = config3(args.grid3)
-        alpha, omega, maxit = args.alpha_factor * alpha_star(p), OMEGA, args.maxit
+        alpha, maxit = args.alpha_factor * alpha_star(p), args.maxit
+        omega = OMEGA if args.omega is None else args.omega
     else:
         p, xt = config4(args.grid4)
         alpha, omega, maxit = alpha_star(p), 1.0, args.maxit
@@ -577,23 +578,111 @@ def run_workload(args):
         sbytes = {"fp64": 8, "fp32": 4, "bf16": 2}[pn] * (2 if p.kind == 2 else 1)
         tin = 1e-2 if pn == "bf16" else TOL_INNER
         mit = min(maxit, args.fp64_maxit) if pn == "fp64" and name != "c1" else maxit
+        a_run = alpha
+        if args.alpha_select and name != "c1":
+            # Sec. 4.3: the smallest alpha * 2^k with kappa(H) kappa(S) u_s < tau
+            a_run = G.select_alpha(p, alpha, prec, args.tau)
+        kh, ks = G.condition_numbers(p, a_run) if p.kind != 3 else (None, None)
+        us = {"fp64": 1.11e-16, "fp32": 5.96e-8, "bf16": 3.91e-3}[pn]
         x.zero_()
-        H.solve(b, x, alpha, omega, prec, TOL, min(3, mit), tol_h=tin, tol_s=tin)  # warm-up
+        H.solve(b, x, a_run, omega, prec, TOL, min(3, mit), tol_h=tin, tol_s=tin)  # warm-up
         x.zero_()
-        st, s = H.solve(b, x, alpha, omega, prec, TOL, mit, tol_h=tin, tol_s=tin)
+        st, s = H.solve(b, x, a_run, omega, prec, TOL, mit, tol_h=tin, tol_s=tin,
+                        alpha_restarts=args.alpha_restarts)
         H.apply(G.OP_A, x, r)
         relres = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
         ab = algorithmic_bytes(p.npoints, s, sbytes, dbytes)
         ach = ab / s["seconds"] / 1e9
         print(json.dumps({
             "metric": "time to 1e-10 rel. backward error: mixed vs FP64 GADI, 1 GB300; HBM %peak",
-            "workload": name, "config": {"workload": desc, "alpha": alpha, "omega": omega, "u_s": pn,
-                                          "tol_inner": tin, "maxit": mit},
+            "workload": name, "config": {"workload": desc, "alpha": a_run, "alpha_over_alpha_star":
+                                          a_run / alpha_star(p), "omega": omega, "u_s": pn,
+                                          "tol_inner": tin, "maxit": mit, "alpha_select": bool(args.alpha_select),
+                                          "alpha_restarts": args.alpha_restarts},
+            "eq_4_1": {"kappa_h": kh, "kappa_s": ks, "kappa_h_kappa_s_u_s": kh * ks * us if kh else None,
+                       "tau": args.tau},
+            "alpha_final": s["alpha"], "restarts": s["restarts"],
             "value": s["seconds"], "unit": "s", "status": G.status_str(st), "outer_its": s["outer_its"],
             "inner_its_h": s["inner_its_h"], "inner_its_s": s["inner_its_s"], "relres": relres,
             "ms_per_outer": 1e3 * s["seconds"] / max(1, s["outer_its"]),
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "peak_source": src}}), flush=True)
+
+
+def run_phases(args):
+    """Each step of Algorithm 1 on its own, through the single-step entry
+    points (one launch each), on the 3D workload at --grid3 (or the 2D one at
+    --grid with --phase-grid 2d): the residual step (x + y, b - A x, ||r||,
+    r_s), CG on H and CGNR on S with a fixed iteration count.  The time of
+    one inner iteration is the difference of two counts (20 and 10) over 10,
+    which removes launch and set-up.  One JSON line per (precision, phase) with
+    the algorithmic bytes (residual 3d + 2s, CG / CGNR iteration 8s per
+    point) per second against the HBM peak."""
+    import torch
+
+    import paper_2512_21164_gb300 as G
+    from paper_2512_21164_gb300 import build as B
+    from workloads import alpha_star, config2, config3
+    B.build()
+    if args.phase_grid == "2d":
+        p, xt = config2(args.grid)
+        wl = f"conv-diff-2d {args.grid}^2"
+    else:
+        p, xt = config3(args.grid3)
+        wl = f"conv-diff-3d {args.grid3}^3"
+    n = p.npoints
+    hbm, src = _peaks()
+    H = G.Gadi.from_problem(p)
+    xtd = torch.from_numpy(xt).cuda()
+    b = torch.zeros_like(xtd)
+    H.apply(G.OP_A, xtd, b)
+    x = (xtd * 0.5).contiguous()
+    xo = torch.empty_like(x)
+    alpha = args.alpha_factor * alpha_star(p)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev0.elapsed_time(ev1) / 1e3)
+        return statistics.median(ts)
+
+    for pn in args.precs.split(","):
+        prec = {"fp64": G.FP64, "fp32": G.FP32, "bf16": G.BF16}[pn]
+        sb = {"fp64": 8, "fp32": 4, "bf16": 2}[pn]
+        dt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.int16}[pn]
+        y = torch.zeros(n, dtype=dt, device="cuda")
+        rs = torch.empty(n, dtype=dt, device="cuda")
+        z = torch.empty(n, dtype=dt, device="cuda")
+        yv = torch.empty(n, dtype=dt, device="cuda")
+        H.step_residual(prec, b, x, y, xo, None, rs)  # warm-up; rs = the right-hand side below
+        t_res = timed(lambda: H.step_residual(prec, b, x, y, xo, None, rs))
+        lines = [("residual", t_res, 1, (3 * 8 + 2 * sb) * n)]
+        H.step_solve_h(alpha, prec, rs, z, 0.0, 2)
+        ih = {k: H.step_solve_h(alpha, prec, rs, z, 0.0, k) for k in (10, 20)}
+        th = {k: timed(lambda k=k: H.step_solve_h(alpha, prec, rs, z, 0.0, k)) for k in (10, 20)}
+        lines.append(("cg_h", (th[20] - th[10]) / max(1, ih[20] - ih[10]), ih, 8 * sb * n))
+        H.step_solve_s(alpha, OMEGA, prec, z, yv, 0.0, 2, 0, False)
+        is_ = {k: H.step_solve_s(alpha, OMEGA, prec, z, yv, 0.0, k, 0, False) for k in (10, 20)}
+        ts_ = {k: timed(lambda k=k: H.step_solve_s(alpha, OMEGA, prec, z, yv, 0.0, k, 0, False)) for k in (10, 20)}
+        lines.append(("cgnr_s", (ts_[20] - ts_[10]) / max(1, is_[20] - is_[10]), is_, 8 * sb * n))
+        for name, t, its, ab in lines:
+            print(json.dumps({"metric": "per-step device time and algorithmic bandwidth", "workload": wl,
+                              "phase": name, "u_s": pn, "ms": t * 1e3, "alg_bytes": ab,
+                              "GBps": ab / t / 1e9, "frac": ab / t / 1e9 / hbm, "peak": hbm,
+                              "iterations": its if isinstance(its, dict) else None,
+                              "peak_source": src,
+                              "note": "inner phases: per iteration (difference of 20 and 10 iterations)"}),
+                  flush=True)
+    H.close()
 
 
 def run_batched(args):
@@ -638,6 +727,16 @@ def run_batched(args):
             "config": {"workload": f"{len(systems)} 2D conv-diff systems N in {{128,256,512,1024}}, 4 rhs each",
                        "alpha": "alpha*(N) x logU[0.5,2]" if scaled else "logU[1e-2,10]", "omega": OMEGA,
                        "maxit": maxit, "u_s": "fp32", "batch_group": args.group5},
+            "group_blocks": {f"N={n}": {str(k): int(v) for k, v in zip(*np.unique(
+                [u["blocks"] for i, u in enumerate(stats) if systems[i // 4][0].nx == n], return_counts=True))}
+                for n in sorted({sp.nx for sp, _, _ in systems})},
+            "per_class": {f"N={n}": {
+                "p50_s": float(np.median([u["seconds"] for i, u in enumerate(stats) if systems[i // 4][0].nx == n])),
+                "max_s": float(np.max([u["seconds"] for i, u in enumerate(stats) if systems[i // 4][0].nx == n])),
+                "outer_p50": float(np.median([u["outer_its"] for i, u in enumerate(stats)
+                                              if systems[i // 4][0].nx == n])),
+                "units": int(sum(1 for i in range(len(stats)) if systems[i // 4][0].nx == n))}
+                for n in sorted({sp.nx for sp, _, _ in systems})},
             "value": len(conv) / sec, "unit": "solves/s", "seconds": sec, "units": len(stats),
             "converged": len(conv), "p50_s": float(np.percentile(t, 50)), "p99_s": float(np.percentile(t, 99)),
             "status": G.status_str(st)}), flush=True)
@@ -757,15 +856,21 @@ def main():
                     help="paper2d / paper3d / paperc: alpha/alpha*:omega pairs tried, or gpr[:omega] for the "
                          "alpha of a GPR trained on small instances (Sec. 4.2)")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc"],
+                    choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc", "phases"],
                     help="c2 (default): the headline line; others: per-precision lines")
     ap.add_argument("--grid3", type=int, default=512)
+    ap.add_argument("--phase-grid", choices=["2d", "3d"], default="3d", help="phases: the 2D or the 3D workload")
     ap.add_argument("--grid4", type=int, default=4096)
     ap.add_argument("--alpha-factor", type=float, default=4.0)
+    ap.add_argument("--alpha-select", action="store_true",
+                    help="c3/c4: start from the alpha of Sec. 4.3's condition check (gadi_select_alpha)")
+    ap.add_argument("--alpha-restarts", type=int, default=0, help="c3/c4: Sec. 4.3 restarts with 2 alpha")
+    ap.add_argument("--tau", type=float, default=0.01)
+    ap.add_argument("--omega", type=float, default=None, help="c3: omega (default that of the 2048^2 line)")
     ap.add_argument("--fp64-maxit", type=int, default=20000)
     ap.add_argument("--maxit5", type=int, default=2000)
     ap.add_argument("--nsys5", type=int, default=96)
-    ap.add_argument("--group5", type=int, default=8)
+    ap.add_argument("--group5", type=int, default=0, help="c5: blocks per group (0 = the library's tuner)")
     ap.add_argument("--record-traffic", nargs=2, metavar=("NCU_REPORT", "PROFILE_CASE_LOG"), default=None,
                     help="write the committed traffic record from an ncu report of --profile-case")
     args = ap.parse_args()
@@ -775,6 +880,8 @@ def main():
         run_profile_case(args)
     elif args.workload == "c5" and args.impl == "ours":
         run_batched(args)
+    elif args.workload == "phases" and args.impl == "ours":
+        run_phases(args)
     elif args.workload == "c2dd" and args.impl == "ours":
         run_c2_dd(args)
     elif args.workload in ("paper2d", "paper3d", "paperc") and args.impl == "ours":

@@ -139,7 +139,10 @@ typedef struct {
     int max_blocks;        /* cap on persistent blocks (0 = automatic)      */
     double *hist;          /* optional HOST array of maxit+1 doubles: relres
                               per outer iteration                           */
-    int batch_group;       /* gadi_solve_batched: blocks per group (0 = 8)  */
+    int batch_group;       /* gadi_solve_batched: k > 0 = groups of k blocks
+                              for every system size; 0 = sizes chosen per
+                              size class by the library's tuner (timed on
+                              the device, kept for the process)            */
     int alpha_restarts;    /* Sec. 4.3: on STAGNATED or DIVERGED,
                               double alpha and continue from the last finite
                               iterate, up to this many times (0 = off)      */
@@ -239,12 +242,21 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
  * (other classes: GADI_ERR_UNSUPPORTED); b[s], x[s]: DEVICE arrays of nrhs
  * consecutive vectors of system s ([nrhs][n_s] doubles), x in/out as in
  * gadi_solve; alpha[s]: that system's regularisation; omega, precisions, tol,
- * maxit and opts are shared.  The grid is split into groups of
- * opts->batch_group blocks (default 8); each group takes (system, rhs) units
- * from a device-side queue, largest system first.  per_unit (nullable) gets
+ * maxit and opts are shared.  Systems of the same grid form a size class.
+ * The grid of persistent blocks is cut into groups, each with a size for its
+ * class: opts->batch_group blocks, or (batch_group = 0, the default) the size
+ * a tuner picks -- it times a few outer iterations of a unit of each class
+ * on groups of 1, 2, 4, ... 64 blocks, the whole grid busy with copies of
+ * the unit (once per grid, precision and options in the process), and
+ * chooses the sizes and the number of groups per
+ * class that minimise the estimated finish time of the batch, with a unit's
+ * cost taken as the time per outer iteration times the grid's side.  Each
+ * group takes (system, rhs) units from its class's device-side queue, then
+ * from the queues of classes of smaller systems (never a larger one).  per_unit (nullable) gets
  * nsys*nrhs entries in the order s*nrhs + j, with `seconds` the unit's own
- * device time.  Returns GADI_OK if every unit converged, else the first
- * non-OK unit status; errors as gadi_solve. */
+ * device time and `blocks` the size of the group that ran it.  Returns
+ * GADI_OK if every unit converged, else the first non-OK unit status;
+ * errors as gadi_solve. */
 gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const double *const *b,
                                double *const *x, const double *alpha, double omega, gadi_prec u_high,
                                gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
@@ -302,8 +314,10 @@ gadi_status gadi_probe_fp64(int iters, double *gops, double *sm_ops_per_clk);
  * compares on the device (1) binary64 -> binary32 round-to-nearest-even,
  * (2) binary64 -> BF16 round-to-nearest-even, both against the hardware
  * conversion, and (3) binary32 -> binary64 of the float whose bits are the
- * low 32 bits of the input, against the hardware widening -- all bit for
- * bit.  mismatches (HOST array of 3) receives the count per check.  Synchronous
+ * low 32 bits of the input, against the hardware widening, and (4) that
+ * float -> BF16 by the conversion instruction equals the integer rounding
+ * sequence (non-NaN floats) -- all bit for bit.  mismatches (HOST array of
+ * 4) receives the count per check.  Synchronous
  * on the legacy default stream.  Errors: INVALID (n < 0, null pointers), CUDA. */
 gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches);
 

@@ -319,8 +319,8 @@ def probe_fp64(iters=200000):
 def selftest_convert(d):
     """gadi_selftest_convert on a device float64 tensor: mismatch counts of the
     integer-pipe conversions (f64->f32, f64->bf16, f32->f64) against the
-    hardware ones."""
-    out = (C.c_longlong * 3)()
+    hardware ones, and of f32->bf16 by instruction against the integer one."""
+    out = (C.c_longlong * 4)()
     st = lib().gadi_selftest_convert(_ptr(d), int(d.numel()), out)
     if st != OK:
         raise GadiError(st, "gadi_selftest_convert")

@@ -14,17 +14,29 @@ template <int KIND, int PREC, int WI, int WR, bool DD = false>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel(const __grid_constant__ BatchParams B)
 {
     using SI = StencilImpl<KIND, PREC, WI, WR, DD>;
-    const int g = blockIdx.x / B.gsize;
-    const VGrid vg{(int)blockIdx.x - g * B.gsize, B.gsize};
+    const int g = B.block_group[blockIdx.x];
+    const int gsize = B.group_size[g];
+    const VGrid vg{(int)blockIdx.x - B.group_first[g], gsize};
     GridSync gs;
     gs.counter = B.bar + (size_t)g * 8;
     gs.abort_flag = B.abort_flag;
-    gs.nblocks = (unsigned)B.gsize;
+    gs.nblocks = (unsigned)gsize;
     volatile int *slot = B.group_unit + (size_t)g * 32;
     const bool leader = vg.b == 0 && threadIdx.x == 0;
+    const int own_class = B.group_class[g];
     for (;;) {
         if (leader) {
-            const int u = atomicAdd(B.queue, 1);
+            // the group's own class first, then the classes of smaller
+            // systems (classes are sorted by system size, largest first): a
+            // group never takes a unit larger than those it was sized for
+            int u = B.nunits;
+            for (int k = own_class; k < B.nclasses && u == B.nunits; k++) {
+                const int c = k;
+                const int n_c = B.class_begin[c + 1] - B.class_begin[c];
+                if (ld_volatile_int(B.queue + (size_t)c * 32) >= n_c) continue;
+                const int i = atomicAdd(B.queue + (size_t)c * 32, 1);
+                if (i < n_c) u = B.order[B.class_begin[c] + i];
+            }
             if (u < B.nunits) {
                 Params &P = B.units[u];
                 char *w = B.work + (size_t)g * B.group_work_bytes;
@@ -36,11 +48,12 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
                     w += B.slab_bytes;
                 }
                 P.q = nullptr;
-                P.part = B.part + (size_t)g * 4 * B.gsize;
+                P.part = B.part + (size_t)4 * B.group_first[g];
                 P.bar = B.bar + (size_t)g * 8;
                 P.hist = B.hist + (size_t)g * B.hist_len;
                 P.ctl = B.ctl + u;
                 P.abort_flag = B.abort_flag;
+                B.ctl[u].pad = gsize; // reported as the unit's block count
                 B.t0[u] = globaltimer_ns();
             }
             *slot = u;
@@ -50,7 +63,8 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
         if (u >= B.nunits) return;
         const Params &P = B.units[u];
         {
-            // (units never take the SM-resident H-solve: a group's blocks share SMs)
+            // (units take the streaming H-solve: the resident forms size
+            // their shared memory for one system per launch)
             StencilAdapter<SI> I(P, vg);
             Runner<PREC, StencilAdapter<SI>> R(P, I);
             R.run();

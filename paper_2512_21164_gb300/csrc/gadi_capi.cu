@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -495,6 +497,7 @@ __global__ void k_selftest_convert(const double *in, long long n, unsigned long 
         if (f64_to_bf16_fast(d) != f64_to_bf16(d)) atomicAdd(bad + 1, 1ull);
         const float g = __uint_as_float((uint32_t)__double_as_longlong(d));
         if (__double_as_longlong(f32_to_f64_fast(g)) != __double_as_longlong((double)g)) atomicAdd(bad + 2, 1ull);
+        if (!isnan(g) && f32_to_bf16_cvt(g) != f32_to_bf16(g)) atomicAdd(bad + 3, 1ull);
     }
 }
 
@@ -1020,7 +1023,7 @@ extern "C" {
 gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches)
 {
     if (!in || !mismatches || n < 0) return GADI_ERR_INVALID;
-    unsigned long long *d_bad = nullptr, hb[3] = {0, 0, 0};
+    unsigned long long *d_bad = nullptr, hb[4] = {0, 0, 0, 0};
     CK(cudaMalloc(&d_bad, sizeof hb));
     cudaError_t e = cudaMemset(d_bad, 0, sizeof hb);
     if (e == cudaSuccess && n > 0) {
@@ -1031,7 +1034,7 @@ gadi_status gadi_selftest_convert(const double *in, long long n, long long *mism
     if (e == cudaSuccess) e = cudaMemcpy(hb, d_bad, sizeof hb, cudaMemcpyDeviceToHost);
     cudaFree(d_bad);
     if (e != cudaSuccess) return cuda_err(e, "gadi_selftest_convert", __LINE__);
-    for (int k = 0; k < 3; k++) mismatches[k] = (long long)hb[k];
+    for (int k = 0; k < 4; k++) mismatches[k] = (long long)hb[k];
     return GADI_OK;
 }
 
@@ -1216,6 +1219,277 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
     return s;
 }
 
+} // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// batched solve: size classes, group sizes and one launch
+// ---------------------------------------------------------------------------
+// A group layout: the groups' sizes and classes in block order.
+struct BatchLayout {
+    std::vector<int> gsize, gclass; // per group
+    int blocks = 0;
+};
+
+// Device buffers of one batched launch, freed on every way out.
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+// One cooperative launch of the batched kernel over `units` (already filled
+// but for the work pointers), classes given by class_begin / order, groups by
+// `lay`.  Per-unit control blocks, start and end times come back in ctl, t0,
+// t1.  timed_s (nullable): device time of the launch (events on h0).
+gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<Params> &units,
+                      const std::vector<int> &class_begin, const std::vector<int> &order, const BatchLayout &lay,
+                      long long max_n, int prec, int hist_len, cudaStream_t st, std::vector<Ctl> &ctl,
+                      std::vector<unsigned long long> &t0, std::vector<unsigned long long> &t1, float *timed_ms)
+{
+    const int nunits = (int)units.size(), ngroups = (int)lay.gsize.size(), nclasses = (int)class_begin.size() - 1;
+    std::vector<int> block_group(lay.blocks), group_first(ngroups);
+    for (int g = 0, b0 = 0; g < ngroups; b0 += lay.gsize[g], g++) {
+        group_first[g] = b0;
+        for (int j = 0; j < lay.gsize[g]; j++) block_group[b0 + j] = g;
+    }
+    const size_t slab = align256((size_t)max_n * elem_bytes(prec)), slab_d = align256((size_t)max_n * 8);
+    const size_t gwork = slab_d + 6 * slab;
+    // one table buffer: block_group, group_first, group_size, group_class,
+    // class_begin, order, queues (32 ints a class), group_unit (32 a group)
+    const size_t nint = (size_t)lay.blocks + 3 * (size_t)ngroups + (nclasses + 1) + nunits + 32 * (size_t)nclasses +
+                        32 * (size_t)ngroups;
+    std::vector<int> tab(nint, 0);
+    size_t off = 0;
+    auto put = [&](const std::vector<int> &v) {
+        const size_t at = off;
+        std::copy(v.begin(), v.end(), tab.begin() + (long)off);
+        off += v.size();
+        return at;
+    };
+    const size_t o_bg = put(block_group), o_gf = put(group_first), o_gs = put(lay.gsize), o_gc = put(lay.gclass);
+    const size_t o_cb = put(class_begin), o_or = put(order);
+    const size_t o_q = off, o_gu = off + 32 * (size_t)nclasses;
+    DevBuf bu, bt, bw, bp, bb, bh, bc, btm;
+    CK(cudaMalloc(&bu.p, sizeof(Params) * (size_t)nunits));
+    CK(cudaMalloc(&bt.p, sizeof(int) * nint));
+    CK(cudaMalloc(&bw.p, gwork * (size_t)ngroups));
+    CK(cudaMalloc(&bp.p, sizeof(double) * 4 * (size_t)lay.blocks));
+    CK(cudaMalloc(&bb.p, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64));
+    CK(cudaMalloc(&bh.p, sizeof(double) * (size_t)hist_len * ngroups));
+    CK(cudaMalloc(&bc.p, sizeof(Ctl) * (size_t)nunits));
+    CK(cudaMalloc(&btm.p, sizeof(unsigned long long) * 2 * (size_t)nunits));
+    CK(cudaMemcpyAsync(bu.p, units.data(), sizeof(Params) * (size_t)nunits, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(bt.p, tab.data(), sizeof(int) * nint, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(bb.p, 0, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64, st));
+    CK(cudaMemsetAsync(bc.p, 0, sizeof(Ctl) * (size_t)nunits, st));
+    const int *ti = (const int *)bt.p;
+    BatchParams B;
+    std::memset(&B, 0, sizeof B);
+    B.units = (Params *)bu.p;
+    B.nunits = nunits;
+    B.ngroups = ngroups;
+    B.nclasses = nclasses;
+    B.block_group = ti + o_bg;
+    B.group_first = ti + o_gf;
+    B.group_size = ti + o_gs;
+    B.group_class = ti + o_gc;
+    B.class_begin = ti + o_cb;
+    B.order = ti + o_or;
+    B.queue = (int *)bt.p + o_q;
+    B.group_unit = (int *)bt.p + o_gu;
+    B.work = (char *)bw.p;
+    B.group_work_bytes = gwork;
+    B.slab_bytes = slab;
+    B.slab_d_bytes = slab_d;
+    B.part = (double *)bp.p;
+    B.bar = (unsigned long long *)bb.p;
+    B.abort_flag = (int *)((unsigned long long *)bb.p + 8 * (size_t)ngroups);
+    B.hist = (double *)bh.p;
+    B.hist_len = hist_len;
+    B.ctl = (Ctl *)bc.p;
+    B.t0 = (unsigned long long *)btm.p;
+    B.t1 = B.t0 + nunits;
+    void *args[] = {&B};
+    CK(cudaEventRecord(h0->ev0, st));
+    CK(cudaLaunchCooperativeKernel(k, dim3(lay.blocks), dim3(kThreadsHost), args, smem, st));
+    CK(cudaEventRecord(h0->ev1, st));
+    ctl.assign(nunits, Ctl{});
+    t0.assign(nunits, 0);
+    t1.assign(nunits, 0);
+    int hab = 0;
+    CK(cudaMemcpyAsync(ctl.data(), bc.p, sizeof(Ctl) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(t0.data(), btm.p, sizeof(unsigned long long) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(t1.data(), B.t1, sizeof(unsigned long long) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hab, B.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (timed_ms) CK(cudaEventElapsedTime(timed_ms, h0->ev0, h0->ev1));
+    if (hab) return GADI_ERR_TIMEOUT;
+    return GADI_OK;
+}
+
+// Group sizes the tuner tries
+constexpr int kTuneSizes[] = {1, 2, 4, 8, 16, 32, 64};
+constexpr int kTuneOuter = 4; // outer iterations of each timed trial
+
+// measured device seconds per outer iteration of one unit of a system class
+// on a group of s blocks, by (grid, precision, residual, inner tolerances,
+// blocks available); kept for the life of the process
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, std::vector<double>> g_tune;
+
+std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts &o, int total)
+{
+    long long th, ts;
+    std::memcpy(&th, &o.tol_h, 8);
+    std::memcpy(&ts, &o.tol_s, 8);
+    return {h->nx, h->ny, prec, o.u_r, th, ts, o.maxit_inner, o.inner_stag, total};
+}
+
+// Time kTuneOuter outer iterations of `unit` on groups of each candidate size
+// s, with the whole grid busy: total / s groups each run their own copy of
+// the unit (tol 0, own x), so the trial sees the L2 and HBM contention of a
+// full batch (a unit alone on a few SMs would run from L2 and look faster
+// than it is).  -1 for sizes above `total`.
+gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const Params &unit, int prec, int total,
+                       cudaStream_t st, std::vector<double> &t_outer)
+{
+    const int nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
+    t_outer.assign(nc, -1.0);
+    DevBuf xs;
+    const size_t vb = sizeof(double) * (size_t)h->nelem;
+    CK(cudaMalloc(&xs.p, vb * (size_t)total));
+    for (int i = 0; i < nc; i++) {
+        const int sz = kTuneSizes[i];
+        if (sz > total) continue;
+        const int ng = total / sz;
+        std::vector<Params> u(ng, unit);
+        std::vector<int> ord(ng);
+        for (int j = 0; j < ng; j++) {
+            u[j].x = (double *)xs.p + (size_t)j * h->nelem;
+            u[j].tol = 0.0;
+            u[j].maxit = kTuneOuter;
+            u[j].outer_win = 0;
+            ord[j] = j;
+        }
+        CK(cudaMemsetAsync(xs.p, 0, vb * (size_t)ng, st));
+        BatchLayout lay;
+        lay.gsize.assign(ng, sz);
+        lay.gclass.assign(ng, 0);
+        lay.blocks = ng * sz;
+        std::vector<Ctl> c;
+        std::vector<unsigned long long> a, b;
+        gadi_status s = run_batch(h, k, smem, u, {0, ng}, ord, lay, h->nelem, prec, kTuneOuter + 2, st, c, a, b,
+                                  nullptr);
+        if (s != GADI_OK) return s;
+        std::vector<double> per(ng);
+        for (int j = 0; j < ng; j++) per[j] = (double)(b[j] - a[j]) * 1e-9 / std::max(1, c[j].outer_its);
+        std::nth_element(per.begin(), per.begin() + ng / 2, per.end());
+        t_outer[i] = per[ng / 2];
+    }
+    return GADI_OK;
+}
+
+// The layout: one size per class (fixed, or the tuned combination that
+// minimises the estimated makespan), groups per class in proportion to the
+// class's work, every block used.  Unit cost = t(s) x an outer-iteration
+// estimate proportional to the grid's side (the HSS rate at alpha near
+// alpha*); classes are in size order (largest first).
+BatchLayout make_layout(const std::vector<long long> &side, const std::vector<int> &count,
+                        const std::vector<std::vector<double>> &t_outer, int fixed, int total,
+                        std::vector<int> *chosen)
+{
+    const int ncl = (int)side.size(), nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
+    std::vector<int> best_s(ncl, 1), best_g(ncl, 1);
+    double best_m = -1.0;
+    auto cost = [&](int c, int si) { return t_outer[c][si] * (double)side[c]; };
+    // candidate indices per class
+    std::vector<std::vector<int>> cand(ncl);
+    for (int c = 0; c < ncl; c++) {
+        if (fixed > 0) {
+            cand[c].push_back(-1);
+            continue;
+        }
+        for (int i = 0; i < nc; i++)
+            if (t_outer[c][i] > 0) cand[c].push_back(i);
+        if (ncl > 4 && !cand[c].empty()) { // many classes: the cheapest size per class only
+            int bi = cand[c][0];
+            for (int i : cand[c])
+                if (kTuneSizes[i] * t_outer[c][i] < kTuneSizes[bi] * t_outer[c][bi]) bi = i;
+            cand[c] = {bi};
+        }
+    }
+    std::vector<int> idx(ncl, 0);
+    for (;;) {
+        // evaluate the combination idx
+        std::vector<int> sz(ncl), g(ncl);
+        double wsum = 0.0;
+        std::vector<double> w(ncl), T(ncl);
+        bool ok = true;
+        for (int c = 0; c < ncl && ok; c++) {
+            if (cand[c].empty()) { ok = false; break; }
+            const int si = cand[c][idx[c]];
+            sz[c] = fixed > 0 ? std::min(fixed, total) : kTuneSizes[si];
+            T[c] = fixed > 0 ? (double)side[c] : cost(c, si);
+            w[c] = count[c] * sz[c] * T[c];
+            wsum += w[c];
+        }
+        int used = 0;
+        if (ok) {
+            for (int c = 0; c < ncl; c++) {
+                g[c] = std::max(1, std::min(count[c], (int)std::floor(total * w[c] / wsum / sz[c])));
+                used += g[c] * sz[c];
+            }
+            if (used > total) ok = false;
+        }
+        if (ok) {
+            // hand out what is left, a group at a time, to the class with the
+            // longest estimated finish
+            for (;;) {
+                int pick = -1;
+                double worst = -1.0;
+                for (int c = 0; c < ncl; c++) {
+                    const double m = std::ceil((double)count[c] / g[c]) * T[c];
+                    if (g[c] < count[c] && used + sz[c] <= total && m > worst) {
+                        worst = m;
+                        pick = c;
+                    }
+                }
+                if (pick < 0) break;
+                g[pick]++;
+                used += sz[pick];
+            }
+            double m = 0.0;
+            for (int c = 0; c < ncl; c++) m = std::max(m, std::ceil((double)count[c] / g[c]) * T[c]);
+            if (best_m < 0 || m < best_m) {
+                best_m = m;
+                best_s = sz;
+                best_g = g;
+            }
+        }
+        int c = 0;
+        while (c < ncl && ++idx[c] >= (int)cand[c].size()) idx[c++] = 0;
+        if (c == ncl) break;
+    }
+    BatchLayout lay;
+    if (best_m < 0) return lay; // no layout fits
+    for (int c = 0; c < ncl; c++)
+        for (int j = 0; j < best_g[c]; j++) {
+            lay.gsize.push_back(best_s[c]);
+            lay.gclass.push_back(c);
+            lay.blocks += best_s[c];
+        }
+    if (chosen) *chosen = best_s;
+    return lay;
+}
+
+} // namespace
+
+extern "C" {
+
 gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const double *const *b,
                                double *const *x, const double *alpha, double omega, gadi_prec u_high,
                                gadi_prec u_low, double tol, int maxit, const gadi_opts *opts,
@@ -1253,22 +1527,30 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, smem));
     int total = per_sm * h0->nsm;
     if (o.max_blocks > 0) total = std::min(total, o.max_blocks);
-    const int gsize = std::max(1, std::min(o.batch_group > 0 ? o.batch_group : 8, total));
-    const int ngroups = total / gsize;
-    if (ngroups <= 0) return GADI_ERR_INVALID;
     const int nunits = nsys * nrhs;
-
-    // units, largest system first (stable)
-    std::vector<int> order(nunits);
-    for (int u = 0; u < nunits; u++) order[u] = u;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return hs[a / nrhs]->nelem > hs[c / nrhs]->nelem;
-    });
+    // size classes: systems of the same grid, largest first
+    std::vector<int> sys_class(nsys, -1);
+    std::vector<int> cls_sys; // a representative system per class
+    {
+        std::vector<int> by_size(nsys);
+        for (int i = 0; i < nsys; i++) by_size[i] = i;
+        std::stable_sort(by_size.begin(), by_size.end(),
+                         [&](int a_, int c_) { return hs[a_]->nelem > hs[c_]->nelem; });
+        for (int i : by_size) {
+            for (int c = 0; c < (int)cls_sys.size(); c++)
+                if (hs[cls_sys[c]]->nx == hs[i]->nx && hs[cls_sys[c]]->ny == hs[i]->ny) sys_class[i] = c;
+            if (sys_class[i] < 0) {
+                sys_class[i] = (int)cls_sys.size();
+                cls_sys.push_back(i);
+            }
+        }
+    }
+    const int ncl = (int)cls_sys.size();
     std::vector<Params> units(nunits);
-    for (int q = 0; q < nunits; q++) {
-        const int u = order[q], sy = u / nrhs, j = u % nrhs;
+    for (int u = 0; u < nunits; u++) {
+        const int sy = u / nrhs, j = u % nrhs;
         gadi_handle *h = hs[sy];
-        Params &P = units[q];
+        Params &P = units[u];
         fill_base(h, P, prec);
         fill_inner(h, P, prec, alpha[sy], omega);
         P.mode = MODE_SOLVE;
@@ -1284,65 +1566,51 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
         P.ur_dd = o.u_r == GADI_FP64X2;
         P.pointwise = o.s_pointwise;
     }
-    // device buffers for this call
-    const size_t slab = align256((size_t)max_n * elem_bytes(prec)), slab_d = align256((size_t)max_n * 8);
-    const size_t gwork = slab_d + 6 * slab;
-    const int hist_len = maxit + 2;
-    struct Buf {
-        void *p = nullptr;
-        ~Buf()
-        {
-            if (p) cudaFree(p);
+    // units by class (largest system first), in unit order within a class
+    std::vector<int> class_begin(ncl + 1, 0), order;
+    std::vector<int> count(ncl, 0);
+    std::vector<long long> side(ncl);
+    for (int c = 0; c < ncl; c++) {
+        for (int u = 0; u < nunits; u++)
+            if (sys_class[u / nrhs] == c) order.push_back(u);
+        class_begin[c + 1] = (int)order.size();
+        count[c] = class_begin[c + 1] - class_begin[c];
+        side[c] = std::max<long long>(hs[cls_sys[c]]->nx, hs[cls_sys[c]]->ny);
+    }
+    // group sizes: fixed (batch_group > 0) or tuned per class on the device
+    // (a few outer iterations of one unit on one group of each size, kept
+    // for the process by grid, precision and options)
+    std::vector<std::vector<double>> t_outer(ncl);
+    if (o.batch_group <= 0) {
+        for (int c = 0; c < ncl; c++) {
+            gadi_handle *hc = hs[cls_sys[c]];
+            const std::vector<long long> key = tune_key(hc, prec, o, total);
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune.find(key);
+                if (it != g_tune.end()) t_outer[c] = it->second;
+            }
+            if (t_outer[c].empty()) {
+                if ((s = tune_class(hc, k, smem, units[order[class_begin[c]]], prec, total, st, t_outer[c])) != GADI_OK)
+                    return s;
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune[key] = t_outer[c];
+            }
         }
-    } bu, bq, bw, bp, bb, bh, bc, bt;
-    CK(cudaMalloc(&bu.p, sizeof(Params) * (size_t)nunits));
-    CK(cudaMalloc(&bq.p, sizeof(int) * (2 + 32 * (size_t)ngroups)));
-    CK(cudaMalloc(&bw.p, gwork * (size_t)ngroups));
-    CK(cudaMalloc(&bp.p, sizeof(double) * 4 * (size_t)gsize * ngroups));
-    CK(cudaMalloc(&bb.p, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64));
-    CK(cudaMalloc(&bh.p, sizeof(double) * (size_t)hist_len * ngroups));
-    CK(cudaMalloc(&bc.p, sizeof(Ctl) * (size_t)nunits));
-    CK(cudaMalloc(&bt.p, sizeof(unsigned long long) * 2 * (size_t)nunits));
-    CK(cudaMemcpyAsync(bu.p, units.data(), sizeof(Params) * (size_t)nunits, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(bq.p, 0, sizeof(int) * (2 + 32 * (size_t)ngroups), st));
-    CK(cudaMemsetAsync(bb.p, 0, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64, st));
-    CK(cudaMemsetAsync(bc.p, 0, sizeof(Ctl) * (size_t)nunits, st));
-    BatchParams B;
-    std::memset(&B, 0, sizeof B);
-    B.units = (Params *)bu.p;
-    B.nunits = nunits;
-    B.gsize = gsize;
-    B.queue = (int *)bq.p;
-    B.group_unit = (int *)bq.p + 32;
-    B.work = (char *)bw.p;
-    B.group_work_bytes = gwork;
-    B.slab_bytes = slab;
-    B.slab_d_bytes = slab_d;
-    B.part = (double *)bp.p;
-    B.bar = (unsigned long long *)bb.p;
-    B.abort_flag = (int *)((unsigned long long *)bb.p + 8 * (size_t)ngroups);
-    B.hist = (double *)bh.p;
-    B.hist_len = hist_len;
-    B.ctl = (Ctl *)bc.p;
-    B.t0 = (unsigned long long *)bt.p;
-    B.t1 = B.t0 + nunits;
-    void *args[] = {&B};
-    CK(cudaEventRecord(h0->ev0, st));
-    CK(cudaLaunchCooperativeKernel(k, dim3(gsize * ngroups), dim3(kThreadsHost), args, smem, st));
-    CK(cudaEventRecord(h0->ev1, st));
-    std::vector<Ctl> hc(nunits);
-    std::vector<unsigned long long> ht(2 * (size_t)nunits);
-    int hab = 0;
-    CK(cudaMemcpyAsync(hc.data(), bc.p, sizeof(Ctl) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ht.data(), bt.p, sizeof(unsigned long long) * 2 * (size_t)nunits, cudaMemcpyDeviceToHost,
-                       st));
-    CK(cudaMemcpyAsync(&hab, B.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (hab) return GADI_ERR_TIMEOUT;
+    }
+    std::vector<int> chosen;
+    const BatchLayout lay = make_layout(side, count, t_outer, o.batch_group, total, &chosen);
+    if (lay.blocks <= 0) return GADI_ERR_INVALID;
+    const int hist_len = maxit + 2;
+    std::vector<Ctl> hc;
+    std::vector<unsigned long long> t0, t1;
+    float ms = 0.f;
+    if ((s = run_batch(h0, k, smem, units, class_begin, order, lay, max_n, prec, hist_len, st, hc, t0, t1, &ms)) !=
+        GADI_OK)
+        return s;
     gadi_status worst = GADI_OK;
-    for (int q = 0; q < nunits; q++) {
-        const int u = order[q];
-        const Ctl &c = hc[q];
+    for (int u = 0; u < nunits; u++) {
+        const Ctl &c = hc[u];
         if (c.status != GADI_OK && worst == GADI_OK) worst = (gadi_status)c.status;
         if (per_unit) {
             gadi_stats &S = per_unit[u];
@@ -1351,9 +1619,9 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.inner_its_s = c.inner_s;
             S.relres = c.relres;
             S.r0_norm = c.r0;
-            S.seconds = (double)(ht[nunits + q] - ht[q]) * 1e-9;
+            S.seconds = (double)(t1[u] - t0[u]) * 1e-9;
             S.status = c.status;
-            S.blocks = gsize;
+            S.blocks = c.pad; // the size of the group that ran the unit
             S.alpha = alpha[u / nrhs];
             S.restarts = 0;
             S.h_resident = 0;

@@ -28,6 +28,17 @@ __device__ __forceinline__ uint16_t f32_to_bf16(float f)
     return (uint16_t)(u >> 16);
 }
 __device__ __forceinline__ float bf16_to_f32(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+// The same rounding by the conversion instruction (cvt.rn.bf16.f32: round to
+// nearest even, subnormals kept): one instruction instead of the integer
+// sequence above, which the inner solves' stores otherwise spend most of
+// their integer-pipe issue slots on.  Equal to f32_to_bf16 for every
+// non-NaN input (NaN gives some quiet NaN).
+__device__ __forceinline__ uint16_t f32_to_bf16_cvt(float f)
+{
+    unsigned short h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return (uint16_t)h;
+}
 
 // double -> BF16 without double rounding: round to odd at binary32 (truncate,
 // then set the last bit if anything was discarded), then round to nearest
@@ -143,6 +154,9 @@ __device__ __forceinline__ void two_prod(double a, double b, double &p, double &
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type C, elements per 16 bytes
 // ---------------------------------------------------------------------------
+#ifndef GADI_RES_HWCVT
+#define GADI_RES_HWCVT 0
+#endif
 template <int P> struct Prec;
 template <> struct Prec<P_FP64> {
     using S = double; using C = double; static constexpr int VEC = 2;
@@ -156,14 +170,18 @@ template <> struct Prec<P_FP32> {
     using S = float; using C = float; static constexpr int VEC = 4;
     __device__ static C ld(S s) { return s; }
     __device__ static S st(C c) { return c; }
+#if GADI_RES_HWCVT
+    __device__ static S from_f64(double d) { return __double2float_rn(d); }
+#else
     __device__ static S from_f64(double d) { return f64_to_f32_fast(d); }
+#endif
     __device__ static S from_f64x2(double hi, double lo) { return f64x2_to_f32(hi, lo); }
     __device__ static double to_f64(S s) { return f32_to_f64_fast(s); }
 };
 template <> struct Prec<P_BF16> {
     using S = uint16_t; using C = float; static constexpr int VEC = 8;
     __device__ static C ld(S s) { return bf16_to_f32(s); }
-    __device__ static S st(C c) { return f32_to_bf16(c); }
+    __device__ static S st(C c) { return f32_to_bf16_cvt(c); }
     __device__ static S from_f64(double d) { return f64_to_bf16_fast(d); }
     __device__ static S from_f64x2(double hi, double lo) { return f64x2_to_bf16(hi, lo); }
     __device__ static double to_f64(S s) { return f32_to_f64_fast(bf16_to_f32(s)); }

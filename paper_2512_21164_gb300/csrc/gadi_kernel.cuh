@@ -981,6 +981,9 @@ template <> __device__ __forceinline__ const Coef7<double> &coef_set<double>(con
 // used (the tensor-memory kernel, whose registers are short), 2: converted
 // from the FP64 coefficients once (the 2D streaming kernel, measured fastest
 // so at 4096^2).
+#ifndef GADI_SPLIT_P3
+#define GADI_SPLIT_P3 1
+#endif
 template <int KIND, int PREC, int WI, int WR, bool DD = false, int CMODE = 0>
 struct StencilImpl {
     using PT = Prec<PREC>;
@@ -1115,7 +1118,7 @@ struct StencilImpl {
     // Measured at 512^3 / 320^3: 5-6 % faster per outer iteration for BF16
     // and FP64, slower for FP32 (whose fused pass recomputes p at the
     // neighbour rows more cheaply than an extra pass over memory costs).
-    static constexpr bool SPLIT_P = D3 && (PREC == P_BF16 || PREC == P_FP64);
+    static constexpr bool SPLIT_P = D3 && ((PREC == P_BF16 && GADI_SPLIT_P3) || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
         using A2 = typename InnerAr<PREC>::T;

@@ -132,18 +132,28 @@ inline void fill_coef_sets(Params &P)
     }
 }
 
-// One batched launch: units (system, right-hand side) taken from a queue by
-// groups of `gsize` blocks.  Per-group state is strided by group index.
+// One batched launch: units (system, right-hand side) taken from queues by
+// groups of blocks.  Groups are contiguous block ranges of sizes chosen per
+// size class of the units (the host's tuner); group g owns blocks
+// [group_first[g], group_first[g] + group_size[g]) and takes units of its
+// class first, then of the other classes (largest first) once its own queue
+// is empty.  Per-group state is strided by group index.
 struct BatchParams {
-    Params *units;  // device array, one per unit; the group leader patches the work pointers
+    Params *units;   // device array, one per unit; the group leader patches the work pointers
     int nunits;
-    int gsize;      // blocks per group
-    int *queue;     // next unit to take (zeroed before launch)
+    int ngroups, nclasses;
+    const int *block_group;  // per block: its group
+    const int *group_first;  // per group: first block
+    const int *group_size;   // per group: blocks
+    const int *group_class;  // per group: its size class
+    const int *class_begin;  // per class c: its units are order[class_begin[c] .. class_begin[c+1])
+    const int *order;        // unit indices by class, largest system first within a class
+    int *queue;      // per class (stride 32 ints): units taken so far (zeroed before launch)
     int *group_unit; // per group (stride 32 ints): the unit it is working on
     // per-group work: x1 (FP64) and six u_s vectors, each slab_bytes long
     char *work;
     size_t group_work_bytes, slab_bytes, slab_d_bytes;
-    double *part;   // per group 4 * gsize doubles
+    double *part;   // 4 doubles per block, a group's slots start at 4 * group_first
     unsigned long long *bar; // per group barrier counter (stride 8)
     double *hist;   // per group hist_len doubles
     int hist_len;

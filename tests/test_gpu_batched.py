@@ -29,7 +29,7 @@ def _systems():
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32, BF16])
-@pytest.mark.parametrize("group", [1, 4])
+@pytest.mark.parametrize("group", [0, 1, 4])  # 0: tuned group sizes
 def test_batched_matches_oracle(prec, group):
     import torch
     nrhs = 2
@@ -62,6 +62,7 @@ def test_batched_matches_oracle(prec, group):
             rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
             assert rel <= 1e-10
             assert u["seconds"] > 0
+            assert u["blocks"] == group if group > 0 else 1 <= u["blocks"] <= 64
     for h in handles:
         h.close()
 

@@ -449,17 +449,17 @@ def test_backward_err_stat_matches_oracle(prec):
     a = 2 * alpha_star(p)
     with G.Gadi.from_problem(p) as H:
         xd = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
-        st, s = H.solve(dev64(b), xd, a, 1.0, prec, 1e-8, 2000, backward_err=100)
+        st, s = H.solve(dev64(b), xd, a, 1.0, prec, 1e-8, 2000, backward_err=400)
         xh = np.zeros(p.nvec)
-        st2, s2 = H.solve(b, xh, a, 1.0, prec, 1e-8, 2000, backward_err=100)
+        st2, s2 = H.solve(b, xh, a, 1.0, prec, 1e-8, 2000, backward_err=400)
         _, s3 = H.solve(b, np.zeros(p.nvec), a, 1.0, prec, 1e-8, 2000)
     assert st == st2 == G.OK and s3["backward_err"] == -1.0
     xg = xd.cpu().numpy()
-    A = orc.dense(O.OP_A) if p.nvec <= 400 else None
-    Anorm = np.linalg.norm(A, 2) if A is not None else O.norm2_power(
-        lambda v: orc.apply(O.OP_A, v), lambda v: orc.apply(O.OP_M, v) - orc.apply(O.OP_N, v), p.nvec, 200)
+    # ||A||_2 exactly (dense SVD): power iteration gives a lower bound of it,
+    # so the reported backward error is at or just above the exact one
+    Anorm = np.linalg.norm(orc.dense(O.OP_A), 2)
     be = O.backward_error(np.linalg.norm(b - orc.apply(O.OP_A, xg)), Anorm, xg, b)
-    assert abs(s["backward_err"] - be) <= 1e-3 * be, (s["backward_err"], be)
+    assert be * (1 - 1e-12) <= s["backward_err"] <= be * (1 + 5e-3), (s["backward_err"], be)
     assert abs(s2["backward_err"] - s["backward_err"]) <= 1e-12 * be
 
 
@@ -477,4 +477,5 @@ def test_diverged_rule_matches_oracle(prec):
     st, sg, xg, hg = _gpu_solve(p, b, 1.0, 0.0, prec, 1e-10, 50, outer_stag_window=0)
     assert so["status"] == "DIVERGED" and st == G.DIVERGED
     assert sg["outer_its"] == so["outer_its"] == 7
-    assert np.allclose(hg, 9.0 ** np.arange(8), rtol=1e-9)
+    # FP32 inner solves round r_s: the closed form then holds to u_s per step
+    assert np.allclose(hg, 9.0 ** np.arange(8), rtol=1e-9 if prec == FP64 else 1e-5)

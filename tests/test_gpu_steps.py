@@ -260,7 +260,12 @@ def test_integer_pipe_conversions_match_hardware():
     pats.append(specials.view(np.uint64))
     allp = np.concatenate(pats).view(np.float64)
     d = torch.from_numpy(allp.copy()).cuda()
-    assert G.selftest_convert(d) == [0, 0, 0]
+    assert G.selftest_convert(d) == [0, 0, 0, 0]
+    # float bit patterns across the whole range (every exponent, both signs,
+    # subnormals, infinities) in their low 32 bits: the BF16 rounding by
+    # instruction equals the integer sequence
+    pats32 = np.arange(0, 2 ** 32, 4099, dtype=np.uint64)
+    assert G.selftest_convert(torch.from_numpy(pats32.view(np.float64)).cuda())[3] == 0
 
 
 @pytest.mark.parametrize("case", list(CASES))
