@@ -247,10 +247,10 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
  * class: opts->batch_group blocks, or (batch_group = 0, the default) the size
  * a tuner picks -- it times a few outer iterations of a unit of each class
  * on groups of 1, 2, 4, ... 64 blocks, the whole grid busy with copies of
- * the unit (once per grid, precision and options in the process), and
- * chooses the sizes and the number of groups per
- * class that minimise the estimated finish time of the batch, with a unit's
- * cost taken as the time per outer iteration times the grid's side.  Each
+ * the unit (once per grid, precision and options in the process), takes
+ * for each class the size with the fewest block-seconds per outer iteration,
+ * and gives each class groups in proportion to its work (units x block-
+ * seconds per outer iteration x the grid's side).  Each
  * group takes (system, rhs) units from its class's device-side queue, then
  * from the queues of classes of smaller systems (never a larger one).  per_unit (nullable) gets
  * nsys*nrhs entries in the order s*nrhs + j, with `seconds` the unit's own
@@ -324,6 +324,13 @@ gadi_status gadi_selftest_convert(const double *in, long long n, long long *mism
 /* y = Op x in FP64 for Op in {A, M, N, A^T} (Sec. 3.1 splitting).  x and y
  * may be host or device memory; stream as in gadi_opts (NULL = default). */
 gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream);
+
+/* The stencil of Op in {A, M, N, A^T} for a stencil problem, as gadi_create
+ * builds it (the operator definition of Sec. 5.2-5.4, h^2-scaled): coef[0]
+ * the centre, coef[1..6] the W, E, S, N, B, T neighbours (zero where the
+ * class has none), coef[7] the imaginary diagonal of the complex class.  Host
+ * only.  Errors: INVALID (CSR, bad sizes or op). */
+gadi_status gadi_stencil_coefs(const gadi_problem *prob, gadi_op op, double *coef);
 
 /* ||A||_2 estimate by `iters` steps of power iteration on A^T A in FP64 on
  * the device (a lower bound; used for the backward error of eq. (3.2)). */

@@ -107,6 +107,8 @@ def lib():
             L.gadi_select_alpha.restype = C.c_int
             L.gadi_selftest_barrier.argtypes = [C.c_int, C.c_double]
             L.gadi_selftest_barrier.restype = C.c_int
+            L.gadi_stencil_coefs.argtypes = [C.POINTER(Problem), C.c_int, dp]
+            L.gadi_stencil_coefs.restype = C.c_int
             L.gadi_probe_sync.argtypes = [C.c_int, C.c_int, dp]
             L.gadi_probe_sync.restype = C.c_int
             L.gadi_probe_fp64.argtypes = [C.c_int, dp, dp]
@@ -339,6 +341,45 @@ def _problem_struct(p):
         P._sig = sg  # keep alive with the struct
         P.sigma_pt = sg.ctypes.data
     return P
+
+
+def stencil_coefs(p, op=OP_A):
+    """gadi_stencil_coefs: [centre, W, E, S, N, B, T, imaginary diagonal] of
+    Op for a workloads.Problem of a stencil class."""
+    out = (C.c_double * 8)()
+    st = lib().gadi_stencil_coefs(C.byref(_problem_struct(p)), int(op), out)
+    if st != OK:
+        raise GadiError(st, "gadi_stencil_coefs")
+    return list(out)
+
+
+def stencil_csr(p, op=OP_A):
+    """The matrix of Op for a real 2D or 3D stencil problem assembled as CSR
+    (host NumPy arrays rowptr, col int32, val float64; columns in increasing
+    order, zero Dirichlet boundary), from the library's own coefficients."""
+    import numpy as np
+    if p.kind not in (STENCIL_2D5, STENCIL_3D7):
+        raise ValueError("real stencil classes only")
+    c = stencil_coefs(p, op)
+    nx, ny, nz = p.nx, p.ny, (p.nz if p.kind == STENCIL_3D7 else 1)
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy, iz = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    # (offset, coefficient, valid mask) in increasing column order
+    terms = []
+    if p.kind == STENCIL_3D7:
+        terms.append((-nx * ny, c[5], iz > 0))
+    terms += [(-nx, c[3], iy > 0), (-1, c[1], ix > 0), (0, c[0], np.ones(n, bool)),
+              (1, c[2], ix < nx - 1), (nx, c[4], iy < ny - 1)]
+    if p.kind == STENCIL_3D7:
+        terms.append((nx * ny, c[6], iz < nz - 1))
+    mask = np.stack([t[2] for t in terms], axis=1)
+    cols = np.stack([idx + t[0] for t in terms], axis=1)
+    vals = np.stack([np.full(n, t[1]) for t in terms], axis=1)
+    counts = mask.sum(axis=1)
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum(counts)
+    return rowptr.astype(np.int32), cols[mask].astype(np.int32), vals[mask].astype(np.float64)
 
 
 def condition_numbers(p, alpha):

@@ -1065,6 +1065,35 @@ gadi_status gadi_selftest_barrier(int nblocks, double timeout_ms)
     return st;
 }
 
+gadi_status gadi_stencil_coefs(const gadi_problem *p, gadi_op op, double *coef)
+{
+    if (!p || !coef || p->kind == GADI_CSR || p->kind < GADI_STENCIL_2D5 || p->kind > GADI_CSR) return GADI_ERR_INVALID;
+    if (op < GADI_OP_A || op > GADI_OP_AT) return GADI_ERR_INVALID;
+    if (p->nx <= 0 || !(p->kappa >= 0) || !std::isfinite(p->h)) return GADI_ERR_INVALID;
+    gadi_handle h;
+    h.kind = p->kind;
+    h.nx = p->nx;
+    h.h = p->h > 0 ? p->h : 1.0 / (p->nx + 1);
+    for (int k = 0; k < 3; k++) h.beta[k] = p->beta[k];
+    h.kappa = p->kappa;
+    h.sigma = p->sigma;
+    stencil_coefs(&h);
+    const Stencil &M = h.M, &N = h.N;
+    Stencil s{};
+    if (op == GADI_OP_A) s = h.A;
+    else if (op == GADI_OP_M) s = M;
+    else if (op == GADI_OP_N) s = N;
+    else {
+        s.d = M.d - N.d;
+        for (int k = 0; k < 6; k++) s.c[k] = M.c[k] - N.c[k];
+        s.e = M.e - N.e;
+    }
+    coef[0] = s.d;
+    for (int k = 0; k < 6; k++) coef[1 + k] = s.c[k];
+    coef[7] = s.e;
+    return GADI_OK;
+}
+
 gadi_status gadi_probe_sync(int nblocks, int iters, double *us_per_sum)
 {
     if (!us_per_sum || iters <= 0 || iters > 1000000) return GADI_ERR_INVALID;
@@ -1333,7 +1362,10 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
 
 // Group sizes the tuner tries
 constexpr int kTuneSizes[] = {1, 2, 4, 8, 16, 32, 64};
-constexpr int kTuneOuter = 4; // outer iterations of each timed trial
+// outer iterations of the two timed trials per size: the cost per outer
+// iteration is taken from their difference, so it is that of the solve's
+// later iterations (the first ones, from x = 0, need fewer inner steps)
+constexpr int kTuneOuterA = 8, kTuneOuterB = 24;
 
 // measured device seconds per outer iteration of one unit of a system class
 // on a group of s blocks, by (grid, precision, residual, inner tolerances,
@@ -1349,11 +1381,12 @@ std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts 
     return {h->nx, h->ny, prec, o.u_r, th, ts, o.maxit_inner, o.inner_stag, total};
 }
 
-// Time kTuneOuter outer iterations of `unit` on groups of each candidate size
-// s, with the whole grid busy: total / s groups each run their own copy of
-// the unit (tol 0, own x), so the trial sees the L2 and HBM contention of a
-// full batch (a unit alone on a few SMs would run from L2 and look faster
-// than it is).  -1 for sizes above `total`.
+// Time outer iterations of `unit` on groups of each candidate size s, with
+// the whole grid busy: total / s groups each run their own copy of the unit
+// (tol 0, own x), so the trial sees the L2 and HBM contention of a full batch
+// (a unit alone on a few SMs would run from L2 and look faster than it is).
+// Two runs (kTuneOuterA and kTuneOuterB outer iterations) give the time per
+// outer iteration by difference.  -1 for sizes above `total`.
 gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const Params &unit, int prec, int total,
                        cudaStream_t st, std::vector<double> &t_outer)
 {
@@ -1366,123 +1399,112 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const Params 
         const int sz = kTuneSizes[i];
         if (sz > total) continue;
         const int ng = total / sz;
-        std::vector<Params> u(ng, unit);
-        std::vector<int> ord(ng);
-        for (int j = 0; j < ng; j++) {
-            u[j].x = (double *)xs.p + (size_t)j * h->nelem;
-            u[j].tol = 0.0;
-            u[j].maxit = kTuneOuter;
-            u[j].outer_win = 0;
-            ord[j] = j;
+        double med[2] = {0.0, 0.0};
+        for (int run = 0; run < 2; run++) {
+            const int outer = run == 0 ? kTuneOuterA : kTuneOuterB;
+            std::vector<Params> u(ng, unit);
+            std::vector<int> ord(ng);
+            for (int j = 0; j < ng; j++) {
+                u[j].x = (double *)xs.p + (size_t)j * h->nelem;
+                u[j].tol = 0.0;
+                u[j].maxit = outer;
+                u[j].outer_win = 0;
+                ord[j] = j;
+            }
+            CK(cudaMemsetAsync(xs.p, 0, vb * (size_t)ng, st));
+            BatchLayout lay;
+            lay.gsize.assign(ng, sz);
+            lay.gclass.assign(ng, 0);
+            lay.blocks = ng * sz;
+            std::vector<Ctl> c;
+            std::vector<unsigned long long> a, b;
+            gadi_status s = run_batch(h, k, smem, u, {0, ng}, ord, lay, h->nelem, prec, outer + 2, st, c, a, b,
+                                      nullptr);
+            if (s != GADI_OK) return s;
+            std::vector<double> per(ng);
+            for (int j = 0; j < ng; j++) per[j] = (double)(b[j] - a[j]) * 1e-9;
+            std::nth_element(per.begin(), per.begin() + ng / 2, per.end());
+            med[run] = per[ng / 2];
         }
-        CK(cudaMemsetAsync(xs.p, 0, vb * (size_t)ng, st));
-        BatchLayout lay;
-        lay.gsize.assign(ng, sz);
-        lay.gclass.assign(ng, 0);
-        lay.blocks = ng * sz;
-        std::vector<Ctl> c;
-        std::vector<unsigned long long> a, b;
-        gadi_status s = run_batch(h, k, smem, u, {0, ng}, ord, lay, h->nelem, prec, kTuneOuter + 2, st, c, a, b,
-                                  nullptr);
-        if (s != GADI_OK) return s;
-        std::vector<double> per(ng);
-        for (int j = 0; j < ng; j++) per[j] = (double)(b[j] - a[j]) * 1e-9 / std::max(1, c[j].outer_its);
-        std::nth_element(per.begin(), per.begin() + ng / 2, per.end());
-        t_outer[i] = per[ng / 2];
+        // (a unit that converged or stopped early in the trial: its time over
+        // the longer run)
+        const double d = (med[1] - med[0]) / (kTuneOuterB - kTuneOuterA);
+        t_outer[i] = d > 0 ? d : med[1] / kTuneOuterB;
     }
     return GADI_OK;
 }
 
-// The layout: one size per class (fixed, or the tuned combination that
-// minimises the estimated makespan), groups per class in proportion to the
-// class's work, every block used.  Unit cost = t(s) x an outer-iteration
-// estimate proportional to the grid's side (the HSS rate at alpha near
-// alpha*); classes are in size order (largest first).
+// The layout: one size per class and groups per class, every block used.
+// Size: fixed, or the tuned size with the fewest block-seconds per outer
+// iteration (s t(s); ties to the larger group, whose units finish sooner).
+// Groups: in proportion to the class's work, units x s t(s) x the grid's
+// side (the outer iteration count of HSS at alpha near alpha* grows with the
+// side), at least one group per class and no more groups than units; blocks
+// left over go, a group at a time, to the class with the longest estimated
+// finish.  Classes are in size order (largest first).
 BatchLayout make_layout(const std::vector<long long> &side, const std::vector<int> &count,
                         const std::vector<std::vector<double>> &t_outer, int fixed, int total,
                         std::vector<int> *chosen)
 {
     const int ncl = (int)side.size(), nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
-    std::vector<int> best_s(ncl, 1), best_g(ncl, 1);
-    double best_m = -1.0;
-    auto cost = [&](int c, int si) { return t_outer[c][si] * (double)side[c]; };
-    // candidate indices per class
-    std::vector<std::vector<int>> cand(ncl);
+    std::vector<int> sz(ncl, 1), g(ncl, 1);
+    std::vector<double> T(ncl, 1.0), w(ncl, 0.0);
+    double wsum = 0.0;
     for (int c = 0; c < ncl; c++) {
         if (fixed > 0) {
-            cand[c].push_back(-1);
-            continue;
+            sz[c] = std::min(fixed, total);
+            // no timings: work in proportion to points x outer iterations
+            T[c] = (double)side[c] * (double)side[c] * (double)side[c] / sz[c];
+        } else {
+            int bi = -1;
+            for (int i = 0; i < nc; i++)
+                if (t_outer[c][i] > 0 &&
+                    (bi < 0 || kTuneSizes[i] * t_outer[c][i] <= kTuneSizes[bi] * t_outer[c][bi] * 1.0000001))
+                    bi = i;
+            if (bi < 0) return BatchLayout{};
+            sz[c] = kTuneSizes[bi];
+            T[c] = t_outer[c][bi] * (double)side[c];
         }
-        for (int i = 0; i < nc; i++)
-            if (t_outer[c][i] > 0) cand[c].push_back(i);
-        if (ncl > 4 && !cand[c].empty()) { // many classes: the cheapest size per class only
-            int bi = cand[c][0];
-            for (int i : cand[c])
-                if (kTuneSizes[i] * t_outer[c][i] < kTuneSizes[bi] * t_outer[c][bi]) bi = i;
-            cand[c] = {bi};
-        }
+        w[c] = count[c] * sz[c] * T[c];
+        wsum += w[c];
     }
-    std::vector<int> idx(ncl, 0);
+    int used = 0;
+    for (int c = 0; c < ncl; c++) {
+        g[c] = std::max(1, std::min(count[c], (int)std::floor(total * w[c] / wsum / sz[c])));
+        used += g[c] * sz[c];
+    }
+    // over the grid (each class takes at least one group): take groups back
+    // from the class with the most, then fail if that is not enough
+    while (used > total) {
+        int pick = -1;
+        for (int c = 0; c < ncl; c++)
+            if (g[c] > 1 && (pick < 0 || g[c] * sz[c] > g[pick] * sz[pick])) pick = c;
+        if (pick < 0) return BatchLayout{};
+        g[pick]--;
+        used -= sz[pick];
+    }
     for (;;) {
-        // evaluate the combination idx
-        std::vector<int> sz(ncl), g(ncl);
-        double wsum = 0.0;
-        std::vector<double> w(ncl), T(ncl);
-        bool ok = true;
-        for (int c = 0; c < ncl && ok; c++) {
-            if (cand[c].empty()) { ok = false; break; }
-            const int si = cand[c][idx[c]];
-            sz[c] = fixed > 0 ? std::min(fixed, total) : kTuneSizes[si];
-            T[c] = fixed > 0 ? (double)side[c] : cost(c, si);
-            w[c] = count[c] * sz[c] * T[c];
-            wsum += w[c];
-        }
-        int used = 0;
-        if (ok) {
-            for (int c = 0; c < ncl; c++) {
-                g[c] = std::max(1, std::min(count[c], (int)std::floor(total * w[c] / wsum / sz[c])));
-                used += g[c] * sz[c];
-            }
-            if (used > total) ok = false;
-        }
-        if (ok) {
-            // hand out what is left, a group at a time, to the class with the
-            // longest estimated finish
-            for (;;) {
-                int pick = -1;
-                double worst = -1.0;
-                for (int c = 0; c < ncl; c++) {
-                    const double m = std::ceil((double)count[c] / g[c]) * T[c];
-                    if (g[c] < count[c] && used + sz[c] <= total && m > worst) {
-                        worst = m;
-                        pick = c;
-                    }
-                }
-                if (pick < 0) break;
-                g[pick]++;
-                used += sz[pick];
-            }
-            double m = 0.0;
-            for (int c = 0; c < ncl; c++) m = std::max(m, std::ceil((double)count[c] / g[c]) * T[c]);
-            if (best_m < 0 || m < best_m) {
-                best_m = m;
-                best_s = sz;
-                best_g = g;
+        int pick = -1;
+        double worst = -1.0;
+        for (int c = 0; c < ncl; c++) {
+            const double m = std::ceil((double)count[c] / g[c]) * T[c];
+            if (g[c] < count[c] && used + sz[c] <= total && m > worst) {
+                worst = m;
+                pick = c;
             }
         }
-        int c = 0;
-        while (c < ncl && ++idx[c] >= (int)cand[c].size()) idx[c++] = 0;
-        if (c == ncl) break;
+        if (pick < 0) break;
+        g[pick]++;
+        used += sz[pick];
     }
     BatchLayout lay;
-    if (best_m < 0) return lay; // no layout fits
     for (int c = 0; c < ncl; c++)
-        for (int j = 0; j < best_g[c]; j++) {
-            lay.gsize.push_back(best_s[c]);
+        for (int j = 0; j < g[c]; j++) {
+            lay.gsize.push_back(sz[c]);
             lay.gclass.push_back(c);
-            lay.blocks += best_s[c];
+            lay.blocks += sz[c];
         }
-    if (chosen) *chosen = best_s;
+    if (chosen) *chosen = sz;
     return lay;
 }
 
@@ -1601,6 +1623,18 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     std::vector<int> chosen;
     const BatchLayout lay = make_layout(side, count, t_outer, o.batch_group, total, &chosen);
     if (lay.blocks <= 0) return GADI_ERR_INVALID;
+    if (const char *v = std::getenv("GADI_TUNE_VERBOSE"); v && *v == '1') {
+        // diagnostic: the tuner's table and the layout taken, on stderr
+        for (int c = 0; c < ncl; c++) {
+            int groups = 0;
+            for (int g : lay.gclass) groups += g == c;
+            std::fprintf(stderr, "gadi batch class %d: %lld x %lld, %d units, size %d, %d groups; s/outer:", c,
+                         (long long)hs[cls_sys[c]]->nx, (long long)hs[cls_sys[c]]->ny, count[c],
+                         chosen.empty() ? 0 : chosen[c], groups);
+            for (size_t i = 0; i < t_outer[c].size(); i++) std::fprintf(stderr, " %g", t_outer[c][i]);
+            std::fprintf(stderr, "\n");
+        }
+    }
     const int hist_len = maxit + 2;
     std::vector<Ctl> hc;
     std::vector<unsigned long long> t0, t1;

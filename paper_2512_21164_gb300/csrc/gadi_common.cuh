@@ -154,9 +154,6 @@ __device__ __forceinline__ void two_prod(double a, double b, double &p, double &
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type C, elements per 16 bytes
 // ---------------------------------------------------------------------------
-#ifndef GADI_RES_HWCVT
-#define GADI_RES_HWCVT 0
-#endif
 template <int P> struct Prec;
 template <> struct Prec<P_FP64> {
     using S = double; using C = double; static constexpr int VEC = 2;
@@ -170,11 +167,7 @@ template <> struct Prec<P_FP32> {
     using S = float; using C = float; static constexpr int VEC = 4;
     __device__ static C ld(S s) { return s; }
     __device__ static S st(C c) { return c; }
-#if GADI_RES_HWCVT
-    __device__ static S from_f64(double d) { return __double2float_rn(d); }
-#else
     __device__ static S from_f64(double d) { return f64_to_f32_fast(d); }
-#endif
     __device__ static S from_f64x2(double hi, double lo) { return f64x2_to_f32(hi, lo); }
     __device__ static double to_f64(S s) { return f32_to_f64_fast(s); }
 };

@@ -649,25 +649,21 @@ struct PhResidual {
             for (int v = 0; v < W; v++) r[v] = __dsub_rn(o.v[0][v], ax[v]);
         }
         S so[W];
-        // ||r_s||^2 is summed in FP32 double-word arithmetic (about 48
-        // significand bits) instead of FP64 -- the square of a u_s value is
-        // formed exactly by a product and its fma error term -- so that the
-        // FP64 pipe carries only the residual itself.  acc[1] holds the pair
-        // (hi, lo) of floats in its two 32-bit halves during the sweep.
-        float hi = __int_as_float(__double2hiint(acc[1])), lo = __int_as_float(__double2loint(acc[1]));
+        // ||r_s||^2 (the start of CG on H, in the inner solve's compute type)
+        // is summed per thread in FP32 like every dot product of the inner
+        // solves, off the FP64 pipe that carries the residual itself; the
+        // per-thread partial travels in the low 32 bits of acc[1] (the high
+        // half stays zero) and is widened for the grid-wide sum.
+        float s2 = __int_as_float(__double2loint(acc[1]));
 #pragma unroll
         for (int v = 0; v < W; v++) {
             acc[0] = fma(r[v], r[v], acc[0]);
             if constexpr (DD) so[v] = PT::from_f64x2(r[v], rl[v]);
             else so[v] = PT::from_f64(r[v]);
             const float sf = PT::ld(so[v]);
-            const float p = __fmul_rn(sf, sf), pe = __fmaf_rn(sf, sf, -p);
-            const float t2 = __fadd_rn(hi, p), bp = __fsub_rn(t2, hi);
-            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t2, bp)), __fsub_rn(p, bp)); // Knuth's TwoSum
-            hi = t2;
-            lo = __fadd_rn(lo, __fadd_rn(err, pe));
+            s2 = __fmaf_rn(sf, sf, s2);
         }
-        acc[1] = __hiloint2double(__float_as_int(hi), __float_as_int(lo));
+        acc[1] = __hiloint2double(0, __float_as_int(s2));
         VecIO<double, W>::store(xo + g, c);
         VecIO<S, W>::store(rs + g, so);
         if (rout) VecIO<double, W>::store(rout + g, r);
@@ -981,9 +977,6 @@ template <> __device__ __forceinline__ const Coef7<double> &coef_set<double>(con
 // used (the tensor-memory kernel, whose registers are short), 2: converted
 // from the FP64 coefficients once (the 2D streaming kernel, measured fastest
 // so at 4096^2).
-#ifndef GADI_SPLIT_P3
-#define GADI_SPLIT_P3 1
-#endif
 template <int KIND, int PREC, int WI, int WR, bool DD = false, int CMODE = 0>
 struct StencilImpl {
     using PT = Prec<PREC>;
@@ -1044,7 +1037,7 @@ struct StencilImpl {
 
     __device__ void residual(const double *xin, const S *y, double *xout, double (&acc)[2]) const
     {
-        double a[2] = {0.0, 0.0}; // a[1]: the float pair (hi, lo), both +0
+        double a[2] = {0.0, 0.0}; // a[1]: the FP32 partial of the r_s norm in its low 32 bits
         PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out, P.sig, P.sig_a};
         ph.dpow2 = P.ad_pow2;
         march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
@@ -1118,7 +1111,7 @@ struct StencilImpl {
     // Measured at 512^3 / 320^3: 5-6 % faster per outer iteration for BF16
     // and FP64, slower for FP32 (whose fused pass recomputes p at the
     // neighbour rows more cheaply than an extra pass over memory costs).
-    static constexpr bool SPLIT_P = D3 && ((PREC == P_BF16 && GADI_SPLIT_P3) || PREC == P_FP64);
+    static constexpr bool SPLIT_P = D3 && (PREC == P_BF16 || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
         using A2 = typename InnerAr<PREC>::T;

@@ -479,3 +479,59 @@ def test_diverged_rule_matches_oracle(prec):
     assert sg["outer_its"] == so["outer_its"] == 7
     # FP32 inner solves round r_s: the closed form then holds to u_s per step
     assert np.allclose(hg, 9.0 ** np.arange(8), rtol=1e-9 if prec == FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+def test_stencil_matrix_as_csr_matches_oracle_and_stencil(prec):
+    """The benchmark's matrix class (2D convection-diffusion, beta drawn by
+    seed 2) assembled as CSR and solved by the CSR kernels: against the
+    oracle's solve of the CSR it assembles from its own coefficients, and
+    against the stencil kernels on the same system (alpha = 8 alpha*,
+    omega = 0, inner tolerances of the precision)."""
+    from test_csr_assembly import oracle_csr
+    from workloads import K_CSR, Problem
+    p, xt = conv_diff_2d(64, 2, ny=48)
+    rp, cl, vl = G.stencil_csr(p)
+    pc = Problem(K_CSR, p.npoints, rowptr=rp, col=cl, val=vl)
+    orp, ocl, ovl = oracle_csr(p)
+    po = Problem(K_CSR, p.npoints, rowptr=orp, col=ocl, val=ovl)
+    orc = O.Oracle(po)
+    b = orc.rhs(xt)
+    alpha = 8 * alpha_star(p)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, alpha, 0.0, prec, tol=1e-10, maxit=20000, tol_h=th, tol_s=ts)
+    st, sg, xg, _ = _gpu_solve(pc, b, alpha, 0.0, prec, 1e-10, 20000)
+    st2, sg2, xg2, _ = _gpu_solve(p, b, alpha, 0.0, prec, 1e-10, 20000)
+    assert so["status"] == "OK" and st == G.OK and st2 == G.OK
+    band = max(2, BAND[prec] * so["outer_its"])
+    assert abs(sg["outer_its"] - so["outer_its"]) <= band, (sg["outer_its"], so["outer_its"])
+    assert abs(sg2["outer_its"] - sg["outer_its"]) <= band, (sg2["outer_its"], sg["outer_its"])
+    for xv in (xg, xg2):
+        rel = np.linalg.norm(b - orc.apply(O.OP_A, xv)) / np.linalg.norm(b)
+        assert rel <= 1e-10, rel
+    fe_o = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+    assert np.linalg.norm(xg - xt) / np.linalg.norm(xt) <= 10 * fe_o + 1e-14
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_config3_twin_matches_oracle(prec):
+    """The 512^3 benchmark's 64^3 twin (beta = (1,1,1) U[1,50] by the same
+    seed, alpha = alpha*, omega = 0, the alpha and omega the 512^3 lines use)
+    against the oracle (its all-core build): outer iterations in the band,
+    relres and backward error <= 1e-10, forward error within 10x."""
+    from workloads import config3
+    p, xt = config3(64)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    alpha = alpha_star(p)
+    omp = O.Oracle(p, omp=True) if O.has_openmp() else orc
+    xo, so = omp.gadi(b, alpha, 0.0, prec, tol=1e-10, maxit=20000, tol_h=1e-3, tol_s=1e-3)
+    st, sg, xg, _ = _gpu_solve(p, b, alpha, 0.0, prec, 1e-10, 20000, backward_err=50)
+    assert so["status"] == "OK" and st == G.OK, (so["status"], G.status_str(st))
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"]), \
+        (sg["outer_its"], so["outer_its"])
+    r = b - orc.apply(O.OP_A, xg)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    assert sg["backward_err"] <= 1e-10
+    fe_o = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+    assert np.linalg.norm(xg - xt) / np.linalg.norm(xt) <= 10 * fe_o + 1e-14
