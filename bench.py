@@ -428,6 +428,7 @@ WORKLOADS = {
     # name: (builder, precisions, alpha factor, omega, maxit, inner tol per precision)
     "c1": ("conv-diff-2d 64x64, beta=(10,10), alpha=0.5, omega=1, maxit 500, plain FP64", ["fp64"]),
     "c3": ("conv-diff-3d 512^3 (n=134217728), beta=(1,1,1)U[1,50] seed 3", ["bf16", "fp32", "fp64"]),
+    "c2s": (WORKLOAD + ", alpha = alpha*, omega = 1 (the untuned closed-form choice)", ["fp32", "fp64"]),
     "c4": ("complex reaction-diffusion 4096^2 (n=16777216 complex), kappa~U[0,10], sigma~U[1,100] seed 4",
            ["bf16", "fp32", "fp64"]),
 }
@@ -572,6 +573,10 @@ def run_workload(args):
     if name == "c1":
         p, xt, c = config1()
         alpha, omega, maxit = c["alpha"], c["omega"], c["maxit"]
+    elif name == "c2s":
+        from workloads import config2
+        p, xt = config2(args.grid)
+        alpha, omega, maxit = alpha_star(p), 1.0, args.maxit
     elif name == "c3":
         p, xt = config3(args.grid3)
         alpha, maxit = args.alpha_factor * alpha_star(p), args.maxit
@@ -786,10 +791,10 @@ def run_batched(args):
             al.append(a)
         maxit = args.maxit5 if not scaled else 20000
         tune_s = None
-        if not scaled:
-            # the group-size tuner runs on the first batch of these grids in
-            # the process (timed here, outside the measured launch); a
-            # 2-iteration batch triggers it
+        if args.group5 <= 0:
+            # the group-size tuner runs on the first batch of these grids and
+            # alpha values in the process (timed here, outside the measured
+            # launch); a 2-iteration batch triggers it
             xw = [torch.zeros_like(v) for v in xs]
             t0 = time.perf_counter()
             G.solve_batched(hs, 4, bs, xw, al, OMEGA, G.FP32, TOL, 2, tol_h=TOL_INNER, tol_s=TOL_INNER,
@@ -940,7 +945,7 @@ def main():
                     help="paper2d / paper3d / paperc: alpha/alpha*:omega pairs tried, or gpr[:omega] for the "
                          "alpha of a GPR trained on small instances (Sec. 4.2)")
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc", "phases", "csr2d"],
+                    choices=["c2", "c1", "c3", "c4", "c5", "c2dd", "paper2d", "paper3d", "paperc", "phases", "csr2d", "c2s"],
                     help="c2 (default): the headline line; others: per-precision lines")
     ap.add_argument("--grid3", type=int, default=512)
     ap.add_argument("--phase-grid", choices=["2d", "3d"], default="3d", help="phases: the 2D or the 3D workload")

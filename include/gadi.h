@@ -245,9 +245,9 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
  * maxit and opts are shared.  Systems of the same grid form a size class.
  * The grid of persistent blocks is cut into groups, each with a size for its
  * class: opts->batch_group blocks, or (batch_group = 0, the default) the size
- * a tuner picks -- it times a few outer iterations of a unit of each class
- * on groups of 1, 2, 4, ... 64 blocks, the whole grid busy with copies of
- * the unit (once per grid, precision and options in the process), takes
+ * a tuner picks -- it times outer iterations of each class's units on groups
+ * of 1, 2, 4, ... 64 blocks, the whole grid busy with copies of them (once
+ * per grid, precision, options and alpha values in the process), takes
  * for each class the size with the fewest block-seconds per outer iteration,
  * and gives each class groups in proportion to its work (units x block-
  * seconds per outer iteration x the grid's side).  Each

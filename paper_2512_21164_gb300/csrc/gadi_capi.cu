@@ -1373,22 +1373,31 @@ constexpr int kTuneOuterA = 8, kTuneOuterB = 24;
 std::mutex g_tune_mu;
 std::map<std::vector<long long>, std::vector<double>> g_tune;
 
-std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts &o, int total)
+// the key: grid, precision, options, blocks, and the class's alpha values
+// (alpha sets the inner iteration counts, hence the cost per outer iteration)
+std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts &o, int total,
+                                const std::vector<double> &alphas)
 {
     long long th, ts;
     std::memcpy(&th, &o.tol_h, 8);
     std::memcpy(&ts, &o.tol_s, 8);
-    return {h->nx, h->ny, prec, o.u_r, th, ts, o.maxit_inner, o.inner_stag, total};
+    std::vector<long long> k = {h->nx, h->ny, prec, o.u_r, th, ts, o.maxit_inner, o.inner_stag, total};
+    for (double a : alphas) {
+        long long b;
+        std::memcpy(&b, &a, 8);
+        k.push_back(b);
+    }
+    return k;
 }
 
-// Time outer iterations of `unit` on groups of each candidate size s, with
-// the whole grid busy: total / s groups each run their own copy of the unit
-// (tol 0, own x), so the trial sees the L2 and HBM contention of a full batch
+// Time outer iterations of the units of a class on groups of each candidate
+// size s, with the whole grid busy: total / s groups each run a copy of one of
+// the class's units (tol 0, own x), so the trial sees the L2 and HBM contention of a full batch
 // (a unit alone on a few SMs would run from L2 and look faster than it is).
 // Two runs (kTuneOuterA and kTuneOuterB outer iterations) give the time per
 // outer iteration by difference.  -1 for sizes above `total`.
-gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const Params &unit, int prec, int total,
-                       cudaStream_t st, std::vector<double> &t_outer)
+gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::vector<Params> &cls, int prec,
+                       int total, cudaStream_t st, std::vector<double> &t_outer)
 {
     const int nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
     t_outer.assign(nc, -1.0);
@@ -1402,9 +1411,12 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const Params 
         double med[2] = {0.0, 0.0};
         for (int run = 0; run < 2; run++) {
             const int outer = run == 0 ? kTuneOuterA : kTuneOuterB;
-            std::vector<Params> u(ng, unit);
+            // the copies cycle through the class's units (their alpha values
+            // and right-hand sides)
+            std::vector<Params> u(ng);
             std::vector<int> ord(ng);
             for (int j = 0; j < ng; j++) {
+                u[j] = cls[(size_t)j % cls.size()];
                 u[j].x = (double *)xs.p + (size_t)j * h->nelem;
                 u[j].tol = 0.0;
                 u[j].maxit = outer;
@@ -1606,14 +1618,20 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     if (o.batch_group <= 0) {
         for (int c = 0; c < ncl; c++) {
             gadi_handle *hc = hs[cls_sys[c]];
-            const std::vector<long long> key = tune_key(hc, prec, o, total);
+            std::vector<Params> cls;
+            std::vector<double> al;
+            for (int q = class_begin[c]; q < class_begin[c + 1]; q++) {
+                cls.push_back(units[order[q]]);
+                al.push_back(alpha[order[q] / nrhs]);
+            }
+            const std::vector<long long> key = tune_key(hc, prec, o, total, al);
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 auto it = g_tune.find(key);
                 if (it != g_tune.end()) t_outer[c] = it->second;
             }
             if (t_outer[c].empty()) {
-                if ((s = tune_class(hc, k, smem, units[order[class_begin[c]]], prec, total, st, t_outer[c])) != GADI_OK)
+                if ((s = tune_class(hc, k, smem, cls, prec, total, st, t_outer[c])) != GADI_OK)
                     return s;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune[key] = t_outer[c];
