@@ -66,6 +66,45 @@ struct CsrImpl {
         if constexpr (sizeof(T) == 8) return __ldcg(x + j);
         else return PT::ld(x[j]);
     }
+    template <class VT, class VP> __device__ static VT ldv(const VP *v, int k)
+    {
+        if constexpr (sizeof(VP) == 8) return (VT)v[k];
+        else return (VT)PT::ld(v[k]);
+    }
+    // Sparse products over the rows, RB rows per thread at a time (rows i,
+    // i + di, ..., a grid stride apart): their row pointers, indices and
+    // gathers are independent loads, so a thread keeps RB rows' loads in
+    // flight instead of one chain of dependent loads.  Each row still sums
+    // its entries in CSR order.  body(row, sum) consumes each row's result.
+    static constexpr int RB = 4;
+    template <class VT, class XT, class AR, class VP, class Body>
+    __device__ void spmv_loop(const int *rp, const int *cl, const VP *val, const XT *x, Body body) const
+    {
+        const long long step = di();
+        for (long long i = i0(); i < n; i += RB * step) {
+            int b[RB], e[RB], len = 0;
+            VT sum[RB];
+#pragma unroll
+            for (int r = 0; r < RB; r++) {
+                const long long row = i + r * step;
+                b[r] = row < n ? rp[row] : 0;
+                e[r] = row < n ? rp[row + 1] : 0;
+                sum[r] = VT(0);
+                len = max(len, e[r] - b[r]);
+            }
+            for (int k = 0; k < len; k++) {
+#pragma unroll
+                for (int r = 0; r < RB; r++)
+                    if (b[r] + k < e[r])
+                        sum[r] = AR::madd(ldv<VT>(val, b[r] + k), (VT)ldx(x, cl[b[r] + k]), sum[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RB; r++) {
+                const long long row = i + r * step;
+                if (row < n) body(row, sum[r]);
+            }
+        }
+    }
 
     __device__ bool residual(const double *xin, const S *y, double *xout, double (&acc)[2],
                              const GridSync &gs) const
@@ -75,6 +114,21 @@ struct CsrImpl {
         if (!gs.sync()) return false;
         double a0 = 0.0, a1 = 0.0;
         S *rs = (S *)P.r;
+        if constexpr (!DD) {
+            spmv_loop<double, double, ArFusedD>(P.rowptr, P.col, P.aval, (const double *)xout,
+                                                [&](long long i, double ax) {
+                const double r = __dsub_rn(P.b[i], ax);
+                const S sv = PT::from_f64(r);
+                a0 = fma(r, r, a0);
+                rs[i] = sv;
+                const double d = PT::to_f64(sv);
+                a1 = fma(d, d, a1);
+                if (P.r_out) P.r_out[i] = r;
+            });
+            acc[0] = a0;
+            acc[1] = a1;
+            return true;
+        }
         for (long long i = i0(); i < n; i += di()) {
             double r, rl = 0.0;
             S sv;
@@ -105,8 +159,8 @@ struct CsrImpl {
     {
         // op selection is done on the host by pointing rowptr/col/aval at
         // the operator to apply
-        for (long long i = i0(); i < n; i += di())
-            yout[i] = spmv_row<double, double, ArFusedD>(P.rowptr, P.col, P.aval, x, (int)i);
+        spmv_loop<double, double, ArFusedD>(P.rowptr, P.col, P.aval, x,
+                                            [&](long long i, double v) { yout[i] = v; });
         return true;
     }
     __device__ bool h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2], const GridSync &gs) const
@@ -121,13 +175,10 @@ struct CsrImpl {
         AT a = AT(0);
         C *q = (C *)P.q;
         const S *hv = (const S *)P.hval;
-        for (long long i = i0(); i < n; i += di()) {
-            C s = C(0);
-            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
-                s = A::madd(PT::ld(hv[k]), PT::ld(pnew[P.mcol[k]]), s);
+        spmv_loop<C, S, A>(P.mrowptr, P.mcol, hv, (const S *)pnew, [&](long long i, C s) {
             q[i] = s;
             a += (AT)PT::ld(pnew[i]) * (AT)s;
-        }
+        });
         acc[0] = a;
         acc[1] = AT(0);
         return true;
@@ -158,15 +209,12 @@ struct CsrImpl {
         S *t = (S *)P.r;
         const S *tv = (const S *)P.tval;
         AT a = AT(0);
-        for (long long i = i0(); i < n; i += di()) {
-            C s = C(0);
-            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
-                s = A::madd(PT::ld(tv[k]), PT::ld(g[P.mcol[k]]), s);
+        spmv_loop<C, S, A>(P.mrowptr, P.mcol, tv, (const S *)g, [&](long long i, C s) {
             const S ts = PT::st(s);
             t[i] = ts;
             const AT x = (AT)PT::ld(ts);
             a += x * x;
-        }
+        });
         acc[0] = a;
         acc[1] = AT(0);
         return true;
@@ -183,15 +231,12 @@ struct CsrImpl {
         S *u = (S *)P.u;
         const S *sv = (const S *)P.sval;
         AT a = AT(0);
-        for (long long i = i0(); i < n; i += di()) {
-            C s = C(0);
-            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
-                s = A::madd(PT::ld(sv[k]), PT::ld(pnew[P.mcol[k]]), s);
+        spmv_loop<C, S, A>(P.mrowptr, P.mcol, sv, (const S *)pnew, [&](long long i, C s) {
             const S us = PT::st(s);
             u[i] = us;
             const AT x = (AT)PT::ld(us);
             a += x * x;
-        }
+        });
         acc[0] = a;
         acc[1] = AT(0);
         return true;
@@ -202,17 +247,14 @@ struct CsrImpl {
         const S *tv = (const S *)P.tval;
         S *y = (S *)P.y, *t = (S *)P.r;
         AT a = AT(0);
-        for (long long i = i0(); i < n; i += di()) {
-            C w = C(0);
-            for (int k = P.mrowptr[i]; k < P.mrowptr[i + 1]; k++)
-                w = A::madd(PT::ld(tv[k]), PT::ld(u[P.mcol[k]]), w);
+        spmv_loop<C, S, A>(P.mrowptr, P.mcol, tv, u, [&](long long i, C w) {
             const C pp = PT::ld(p[i]);
             y[i] = PT::st(first ? A::mul(a_, pp) : A::madd(a_, pp, PT::ld(y[i])));
             const S tn = PT::st(A::madd(-a_, w, PT::ld(t[i])));
             t[i] = tn;
             const AT x = (AT)PT::ld(tn);
             a += x * x;
-        }
+        });
         acc[0] = a;
         acc[1] = AT(0);
         return true;
