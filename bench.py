@@ -798,12 +798,13 @@ def run_batched(args):
             xw = [torch.zeros_like(v) for v in xs]
             t0 = time.perf_counter()
             G.solve_batched(hs, 4, bs, xw, al, OMEGA, G.FP32, TOL, 2, tol_h=TOL_INNER, tol_s=TOL_INNER,
-                            batch_group=args.group5)
+                            batch_group=args.group5, batch_interleave=args.interleave5)
             tune_s = time.perf_counter() - t0
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record()
-        st, stats = G.solve_batched(hs, 4, bs, xs, al, OMEGA, G.FP32, TOL, maxit, tol_h=TOL_INNER,
+        st, stats = G.solve_batched(hs, 4, bs, xs, al, OMEGA, G.FP32, TOL, maxit, batch_interleave=args.interleave5,
+                                    tol_h=TOL_INNER,
                                     tol_s=TOL_INNER, batch_group=args.group5)
         ev1.record()
         torch.cuda.synchronize()
@@ -814,7 +815,8 @@ def run_batched(args):
             "metric": "batched GADI solves/s (time to 1e-10 per unit)", "workload": "c5",
             "config": {"workload": f"{len(systems)} 2D conv-diff systems N in {{128,256,512,1024}}, 4 rhs each",
                        "alpha": "alpha*(N) x logU[0.5,2]" if scaled else "logU[1e-2,10]", "omega": OMEGA,
-                       "maxit": maxit, "u_s": "fp32", "batch_group": args.group5},
+                       "maxit": maxit, "u_s": "fp32", "batch_group": args.group5,
+                       "interleaved_rhs": bool(args.interleave5)},
             "group_blocks": {f"N={n}": {str(k): int(v) for k, v in zip(*np.unique(
                 [u["blocks"] for i, u in enumerate(stats) if systems[i // 4][0].nx == n], return_counts=True))}
                 for n in sorted({sp.nx for sp, _, _ in systems})},
@@ -959,6 +961,7 @@ def main():
     ap.add_argument("--fp64-maxit", type=int, default=20000)
     ap.add_argument("--maxit5", type=int, default=2000)
     ap.add_argument("--nsys5", type=int, default=96)
+    ap.add_argument("--interleave5", type=int, default=0, help="c5: 1 = the four right-hand sides of a system in one unit")
     ap.add_argument("--group5", type=int, default=0, help="c5: blocks per group (0 = the library's tuner)")
     ap.add_argument("--record-traffic", nargs=2, metavar=("NCU_REPORT", "PROFILE_CASE_LOG"), default=None,
                     help="write the committed traffic record from an ncu report of --profile-case")

@@ -124,7 +124,7 @@ typedef struct {
  * s_pointwise = 1, stream = NULL, max_blocks = 0 (one persistent block set
  * per SM), hist = NULL, batch_group = 0, alpha_restarts = 0, h_resident = 2
  * (1 for BF16, where tensor memory measured slower), u_r = GADI_FP64,
- * s_resident = 1, backward_err = 0.  The
+ * s_resident = 1, backward_err = 0, batch_interleave = 0.  The
  * step entry gadi_step_solve_h takes the same h_resident default. */
 typedef struct {
     double tol_h;          /* inner CG relative residual tolerance on H     */
@@ -176,6 +176,16 @@ typedef struct {
                               from k steps of gadi_norm2_estimate (kept by
                               the handle for the next solve with the same
                               k); outside the timed solve.  < 0: INVALID.  */
+    int batch_interleave;  /* gadi_solve_batched with nrhs = 4, FP32 inner
+                              solves and an FP64 residual: 1 = the four
+                              right-hand sides of a system form one unit,
+                              their vectors interleaved as [n][4] (one
+                              sweep, barrier and grid sum serve all four;
+                              each keeps its own scalars and stopping);
+                              0 = one unit per right-hand side (the
+                              default: faster on uneven batches whose
+                              large systems dominate).  Other values:
+                              INVALID.                                   */
 } gadi_opts;
 
 typedef struct {
@@ -247,12 +257,15 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
  * class: opts->batch_group blocks, or (batch_group = 0, the default) the size
  * a tuner picks -- it times outer iterations of each class's units on groups
  * of 1, 2, 4, ... 64 blocks, the whole grid busy with copies of them (once
- * per grid, precision, options and alpha values in the process), takes
- * for each class the size with the fewest block-seconds per outer iteration,
- * and gives each class groups in proportion to its work (units x block-
- * seconds per outer iteration x the grid's side).  Each
- * group takes (system, rhs) units from its class's device-side queue, then
- * from the queues of classes of smaller systems (never a larger one).  per_unit (nullable) gets
+ * per grid, precision, options and alpha values in the process), starts
+ * each class at the size with the fewest block-seconds per outer iteration,
+ * gives each class groups in proportion to its work (units x block-seconds
+ * per outer iteration x the grid's side), then moves one class at a time to
+ * the size that most lowers the estimated finish time of the batch.  Each
+ * group takes units from its class's device-side queue, then from the
+ * queues of classes of smaller systems (never a larger one).  A unit is one
+ * (system, rhs), or with opts->batch_interleave one system's four right-hand
+ * sides.  per_unit (nullable) gets
  * nsys*nrhs entries in the order s*nrhs + j, with `seconds` the unit's own
  * device time and `blocks` the size of the group that ran it.  Returns
  * GADI_OK if every unit converged, else the first non-OK unit status;

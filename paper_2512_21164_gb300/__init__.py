@@ -49,7 +49,7 @@ class Opts(C.Structure):
                 ("s_pointwise", C.c_int), ("stream", C.c_void_p), ("max_blocks", C.c_int),
                 ("hist", C.c_void_p), ("batch_group", C.c_int), ("alpha_restarts", C.c_int),
                 ("h_resident", C.c_int), ("u_r", C.c_int), ("s_resident", C.c_int),
-                ("backward_err", C.c_int)]
+                ("backward_err", C.c_int), ("batch_interleave", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -2,9 +2,16 @@
 // kernel itself is in gadi_batched.cuh).
 #include "gadi.h"
 #include "gadi_batched.cuh"
+#include "gadi_multi.cuh"
 #include "gadi_inst.h"
 
 namespace gadi {
+
+const void *kernel_batched4_2d5(size_t *smem)
+{
+    *smem = 0;
+    return (const void *)gadi_batched4_kernel;
+}
 
 const void *kernel_batched_2d5(int prec, int vec, size_t *smem, int dd)
 {

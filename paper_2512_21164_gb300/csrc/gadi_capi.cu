@@ -651,6 +651,7 @@ gadi_status opts_check(const gadi_opts &o)
     if (o.s_resident != 0 && o.s_resident != 1) return GADI_ERR_INVALID;
     if (o.u_r != GADI_FP64 && o.u_r != GADI_FP64X2) return GADI_ERR_INVALID;
     if (o.backward_err < 0) return GADI_ERR_INVALID;
+    if (o.batch_interleave != 0 && o.batch_interleave != 1) return GADI_ERR_INVALID;
     return GADI_OK;
 }
 
@@ -680,6 +681,7 @@ void gadi_opts_default(gadi_opts *o, gadi_prec u_low)
     o->h_resident = (u_low == GADI_BF16) ? 1 : 2;
     o->u_r = GADI_FP64;
     o->s_resident = 1;
+    o->batch_interleave = 0;
 }
 
 const char *gadi_last_error(void) { return g_last_error; }
@@ -1277,16 +1279,21 @@ struct DevBuf {
 gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<Params> &units,
                       const std::vector<int> &class_begin, const std::vector<int> &order, const BatchLayout &lay,
                       long long max_n, int prec, int hist_len, cudaStream_t st, std::vector<Ctl> &ctl,
-                      std::vector<unsigned long long> &t0, std::vector<unsigned long long> &t1, float *timed_ms)
+                      std::vector<unsigned long long> &t0, std::vector<unsigned long long> &t1, float *timed_ms,
+                      int nr = 1)
 {
+    // nr = 4: units of four interleaved right-hand sides (gadi_batched4_kernel):
+    // 4x the vectors, a third FP64 work vector, 4 control blocks and 4
+    // histories per unit, 16 partial sums per block
     const int nunits = (int)units.size(), ngroups = (int)lay.gsize.size(), nclasses = (int)class_begin.size() - 1;
     std::vector<int> block_group(lay.blocks), group_first(ngroups);
     for (int g = 0, b0 = 0; g < ngroups; b0 += lay.gsize[g], g++) {
         group_first[g] = b0;
         for (int j = 0; j < lay.gsize[g]; j++) block_group[b0 + j] = g;
     }
-    const size_t slab = align256((size_t)max_n * elem_bytes(prec)), slab_d = align256((size_t)max_n * 8);
-    const size_t gwork = slab_d + 6 * slab;
+    const size_t slab = align256((size_t)max_n * nr * elem_bytes(prec)), slab_d = align256((size_t)max_n * nr * 8);
+    const size_t gwork = (nr == 1 ? 1 : 3) * slab_d + 6 * slab;
+    const size_t nctl = (size_t)nunits * nr;
     // one table buffer: block_group, group_first, group_size, group_class,
     // class_begin, order, queues (32 ints a class), group_unit (32 a group)
     const size_t nint = (size_t)lay.blocks + 3 * (size_t)ngroups + (nclasses + 1) + nunits + 32 * (size_t)nclasses +
@@ -1306,15 +1313,15 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
     CK(cudaMalloc(&bu.p, sizeof(Params) * (size_t)nunits));
     CK(cudaMalloc(&bt.p, sizeof(int) * nint));
     CK(cudaMalloc(&bw.p, gwork * (size_t)ngroups));
-    CK(cudaMalloc(&bp.p, sizeof(double) * 4 * (size_t)lay.blocks));
+    CK(cudaMalloc(&bp.p, sizeof(double) * 4 * nr * (size_t)lay.blocks));
     CK(cudaMalloc(&bb.p, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64));
-    CK(cudaMalloc(&bh.p, sizeof(double) * (size_t)hist_len * ngroups));
-    CK(cudaMalloc(&bc.p, sizeof(Ctl) * (size_t)nunits));
+    CK(cudaMalloc(&bh.p, sizeof(double) * (size_t)hist_len * nr * ngroups));
+    CK(cudaMalloc(&bc.p, sizeof(Ctl) * nctl));
     CK(cudaMalloc(&btm.p, sizeof(unsigned long long) * 2 * (size_t)nunits));
     CK(cudaMemcpyAsync(bu.p, units.data(), sizeof(Params) * (size_t)nunits, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(bt.p, tab.data(), sizeof(int) * nint, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(bb.p, 0, sizeof(unsigned long long) * 8 * (size_t)ngroups + 64, st));
-    CK(cudaMemsetAsync(bc.p, 0, sizeof(Ctl) * (size_t)nunits, st));
+    CK(cudaMemsetAsync(bc.p, 0, sizeof(Ctl) * nctl, st));
     const int *ti = (const int *)bt.p;
     BatchParams B;
     std::memset(&B, 0, sizeof B);
@@ -1346,11 +1353,11 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
     CK(cudaEventRecord(h0->ev0, st));
     CK(cudaLaunchCooperativeKernel(k, dim3(lay.blocks), dim3(kThreadsHost), args, smem, st));
     CK(cudaEventRecord(h0->ev1, st));
-    ctl.assign(nunits, Ctl{});
+    ctl.assign(nctl, Ctl{});
     t0.assign(nunits, 0);
     t1.assign(nunits, 0);
     int hab = 0;
-    CK(cudaMemcpyAsync(ctl.data(), bc.p, sizeof(Ctl) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctl.data(), bc.p, sizeof(Ctl) * nctl, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(t0.data(), btm.p, sizeof(unsigned long long) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(t1.data(), B.t1, sizeof(unsigned long long) * (size_t)nunits, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&hab, B.abort_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1397,12 +1404,12 @@ std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts 
 // Two runs (kTuneOuterA and kTuneOuterB outer iterations) give the time per
 // outer iteration by difference.  -1 for sizes above `total`.
 gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::vector<Params> &cls, int prec,
-                       int total, cudaStream_t st, std::vector<double> &t_outer)
+                       int total, cudaStream_t st, std::vector<double> &t_outer, int nr = 1)
 {
     const int nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
     t_outer.assign(nc, -1.0);
     DevBuf xs;
-    const size_t vb = sizeof(double) * (size_t)h->nelem;
+    const size_t vb = sizeof(double) * (size_t)h->nelem * nr; // one unit's x (nr right-hand sides)
     CK(cudaMalloc(&xs.p, vb * (size_t)total));
     for (int i = 0; i < nc; i++) {
         const int sz = kTuneSizes[i];
@@ -1417,7 +1424,7 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::ve
             std::vector<int> ord(ng);
             for (int j = 0; j < ng; j++) {
                 u[j] = cls[(size_t)j % cls.size()];
-                u[j].x = (double *)xs.p + (size_t)j * h->nelem;
+                u[j].x = (double *)xs.p + (size_t)j * h->nelem * nr;
                 u[j].tol = 0.0;
                 u[j].maxit = outer;
                 u[j].outer_win = 0;
@@ -1431,7 +1438,7 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::ve
             std::vector<Ctl> c;
             std::vector<unsigned long long> a, b;
             gadi_status s = run_batch(h, k, smem, u, {0, ng}, ord, lay, h->nelem, prec, outer + 2, st, c, a, b,
-                                      nullptr);
+                                      nullptr, nr);
             if (s != GADI_OK) return s;
             std::vector<double> per(ng);
             for (int j = 0; j < ng; j++) per[j] = (double)(b[j] - a[j]) * 1e-9;
@@ -1454,44 +1461,29 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::ve
 // side), at least one group per class and no more groups than units; blocks
 // left over go, a group at a time, to the class with the longest estimated
 // finish.  Classes are in size order (largest first).
-BatchLayout make_layout(const std::vector<long long> &side, const std::vector<int> &count,
-                        const std::vector<std::vector<double>> &t_outer, int fixed, int total,
-                        std::vector<int> *chosen)
+// Groups per class for a given group size per class: in proportion to each
+// class's work (units x block-seconds per unit), at least one each, then one
+// at a time to the class that would finish last while the grid has room.
+// Returns false if the classes' single groups do not fit in the grid.
+bool assign_groups(const std::vector<int> &sz, const std::vector<double> &T, const std::vector<int> &count,
+                   int total, std::vector<int> &g)
 {
-    const int ncl = (int)side.size(), nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
-    std::vector<int> sz(ncl, 1), g(ncl, 1);
-    std::vector<double> T(ncl, 1.0), w(ncl, 0.0);
+    const int ncl = (int)sz.size();
+    g.assign(ncl, 1);
     double wsum = 0.0;
-    for (int c = 0; c < ncl; c++) {
-        if (fixed > 0) {
-            sz[c] = std::min(fixed, total);
-            // no timings: work in proportion to points x outer iterations
-            T[c] = (double)side[c] * (double)side[c] * (double)side[c] / sz[c];
-        } else {
-            int bi = -1;
-            for (int i = 0; i < nc; i++)
-                if (t_outer[c][i] > 0 &&
-                    (bi < 0 || kTuneSizes[i] * t_outer[c][i] <= kTuneSizes[bi] * t_outer[c][bi] * 1.0000001))
-                    bi = i;
-            if (bi < 0) return BatchLayout{};
-            sz[c] = kTuneSizes[bi];
-            T[c] = t_outer[c][bi] * (double)side[c];
-        }
-        w[c] = count[c] * sz[c] * T[c];
-        wsum += w[c];
-    }
+    std::vector<double> w(ncl);
+    for (int c = 0; c < ncl; c++) wsum += (w[c] = count[c] * sz[c] * T[c]);
     int used = 0;
     for (int c = 0; c < ncl; c++) {
         g[c] = std::max(1, std::min(count[c], (int)std::floor(total * w[c] / wsum / sz[c])));
         used += g[c] * sz[c];
     }
-    // over the grid (each class takes at least one group): take groups back
-    // from the class with the most, then fail if that is not enough
+    // over the grid: take groups back from the class with the most blocks
     while (used > total) {
         int pick = -1;
         for (int c = 0; c < ncl; c++)
             if (g[c] > 1 && (pick < 0 || g[c] * sz[c] > g[pick] * sz[pick])) pick = c;
-        if (pick < 0) return BatchLayout{};
+        if (pick < 0) return false;
         g[pick]--;
         used -= sz[pick];
     }
@@ -1509,6 +1501,82 @@ BatchLayout make_layout(const std::vector<long long> &side, const std::vector<in
         g[pick]++;
         used += sz[pick];
     }
+    return true;
+}
+
+// Estimated finish time of a layout: the class whose units, taken in rounds
+// of its group count, end last (stealing across classes only shortens it).
+double finish_estimate(const std::vector<int> &g, const std::vector<double> &T, const std::vector<int> &count)
+{
+    double m = 0.0;
+    for (size_t c = 0; c < g.size(); c++) m = std::max(m, std::ceil((double)count[c] / g[c]) * T[c]);
+    return m;
+}
+
+BatchLayout make_layout(const std::vector<long long> &side, const std::vector<int> &count,
+                        const std::vector<std::vector<double>> &t_outer, int fixed, int total,
+                        std::vector<int> *chosen, double *estimate)
+{
+    const int ncl = (int)side.size(), nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
+    std::vector<int> sz(ncl, 1), g;
+    std::vector<double> T(ncl, 1.0);
+    // a unit's time on a group of kTuneSizes[i] blocks: the class's time per
+    // outer iteration times the grid's side (the outer iteration count of HSS
+    // near alpha* grows with the side)
+    auto unit_time = [&](int c, int i) { return t_outer[c][i] * (double)side[c]; };
+    std::vector<int> bi(ncl, -1);
+    for (int c = 0; c < ncl; c++) {
+        if (fixed > 0) {
+            sz[c] = std::min(fixed, total);
+            // no timings: work in proportion to points x outer iterations
+            T[c] = (double)side[c] * (double)side[c] * (double)side[c] / sz[c];
+            continue;
+        }
+        // start from the size with the fewest block-seconds per unit
+        for (int i = 0; i < nc; i++)
+            if (t_outer[c][i] > 0 &&
+                (bi[c] < 0 || kTuneSizes[i] * t_outer[c][i] <= kTuneSizes[bi[c]] * t_outer[c][bi[c]] * 1.0000001))
+                bi[c] = i;
+        if (bi[c] < 0) return BatchLayout{};
+        sz[c] = kTuneSizes[bi[c]];
+        T[c] = unit_time(c, bi[c]);
+    }
+    bool ok = assign_groups(sz, T, count, total, g);
+    double best = ok ? finish_estimate(g, T, count) : HUGE_VAL;
+    if (fixed <= 0) {
+        // then one class at a time to the size that lowers the estimated
+        // finish time most, until no change helps (a class with little work
+        // whose cheapest size is large otherwise holds blocks the classes
+        // with the work need, and a class of few large units may finish
+        // sooner on fewer, larger groups)
+        for (int round = 0; round < 8 * ncl + 8; round++) {
+            int bc = -1, bsz = -1;
+            double bt = 0.0, bval = best;
+            for (int c = 0; c < ncl; c++)
+                for (int i = 0; i < nc; i++) {
+                    if (t_outer[c][i] <= 0 || kTuneSizes[i] == sz[c] || kTuneSizes[i] > total) continue;
+                    std::vector<int> s2 = sz, g2;
+                    std::vector<double> T2 = T;
+                    s2[c] = kTuneSizes[i];
+                    T2[c] = unit_time(c, i);
+                    if (!assign_groups(s2, T2, count, total, g2)) continue;
+                    const double e = finish_estimate(g2, T2, count);
+                    if (e < bval * 0.999) {
+                        bval = e;
+                        bc = c;
+                        bsz = kTuneSizes[i];
+                        bt = T2[c];
+                    }
+                }
+            if (bc < 0) break;
+            sz[bc] = bsz;
+            T[bc] = bt;
+            best = bval;
+            ok = true;
+        }
+        ok = assign_groups(sz, T, count, total, g);
+    }
+    if (!ok) return BatchLayout{};
     BatchLayout lay;
     for (int c = 0; c < ncl; c++)
         for (int j = 0; j < g[c]; j++) {
@@ -1517,6 +1585,7 @@ BatchLayout make_layout(const std::vector<long long> &side, const std::vector<in
             lay.blocks += sz[c];
         }
     if (chosen) *chosen = sz;
+    if (estimate) *estimate = finish_estimate(g, T, count);
     return lay;
 }
 
@@ -1554,14 +1623,19 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     gadi_handle *h0 = hs[0];
     cudaStream_t st = (cudaStream_t)o.stream;
     size_t smem = 0;
-    const void *k = kernel_batched_2d5(prec, vec ? 1 : 0, &smem, o.u_r == GADI_FP64X2);
+    // four right-hand sides of a system interleaved in one unit ([n][4]
+    // vectors, FP32 inner solves), or a unit per right-hand side
+    const bool inter = nrhs == 4 && prec == P_FP32 && o.u_r == GADI_FP64 && o.batch_interleave != 0;
+    const int nr = inter ? 4 : 1;
+    const void *k = inter ? kernel_batched4_2d5(&smem) : kernel_batched_2d5(prec, vec ? 1 : 0, &smem, o.u_r == GADI_FP64X2);
     if (!k) return GADI_ERR_UNSUPPORTED;
     if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, smem));
     int total = per_sm * h0->nsm;
     if (o.max_blocks > 0) total = std::min(total, o.max_blocks);
-    const int nunits = nsys * nrhs;
+    const int nunits = inter ? nsys : nsys * nrhs;
+    auto sys_of = [&](int u) { return inter ? u : u / nrhs; };
     // size classes: systems of the same grid, largest first
     std::vector<int> sys_class(nsys, -1);
     std::vector<int> cls_sys; // a representative system per class
@@ -1582,7 +1656,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     const int ncl = (int)cls_sys.size();
     std::vector<Params> units(nunits);
     for (int u = 0; u < nunits; u++) {
-        const int sy = u / nrhs, j = u % nrhs;
+        const int sy = sys_of(u), j = inter ? 0 : u % nrhs;
         gadi_handle *h = hs[sy];
         Params &P = units[u];
         fill_base(h, P, prec);
@@ -1606,7 +1680,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     std::vector<long long> side(ncl);
     for (int c = 0; c < ncl; c++) {
         for (int u = 0; u < nunits; u++)
-            if (sys_class[u / nrhs] == c) order.push_back(u);
+            if (sys_class[sys_of(u)] == c) order.push_back(u);
         class_begin[c + 1] = (int)order.size();
         count[c] = class_begin[c + 1] - class_begin[c];
         side[c] = std::max<long long>(hs[cls_sys[c]]->nx, hs[cls_sys[c]]->ny);
@@ -1622,16 +1696,17 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             std::vector<double> al;
             for (int q = class_begin[c]; q < class_begin[c + 1]; q++) {
                 cls.push_back(units[order[q]]);
-                al.push_back(alpha[order[q] / nrhs]);
+                al.push_back(alpha[sys_of(order[q])]);
             }
-            const std::vector<long long> key = tune_key(hc, prec, o, total, al);
+            std::vector<long long> key = tune_key(hc, prec, o, total, al);
+            key.push_back(nr);
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 auto it = g_tune.find(key);
                 if (it != g_tune.end()) t_outer[c] = it->second;
             }
             if (t_outer[c].empty()) {
-                if ((s = tune_class(hc, k, smem, cls, prec, total, st, t_outer[c])) != GADI_OK)
+                if ((s = tune_class(hc, k, smem, cls, prec, total, st, t_outer[c], nr)) != GADI_OK)
                     return s;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune[key] = t_outer[c];
@@ -1639,7 +1714,8 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
         }
     }
     std::vector<int> chosen;
-    const BatchLayout lay = make_layout(side, count, t_outer, o.batch_group, total, &chosen);
+    double est = 0.0;
+    const BatchLayout lay = make_layout(side, count, t_outer, o.batch_group, total, &chosen, &est);
     if (lay.blocks <= 0) return GADI_ERR_INVALID;
     if (const char *v = std::getenv("GADI_TUNE_VERBOSE"); v && *v == '1') {
         // diagnostic: the tuner's table and the layout taken, on stderr
@@ -1652,20 +1728,23 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             for (size_t i = 0; i < t_outer[c].size(); i++) std::fprintf(stderr, " %g", t_outer[c][i]);
             std::fprintf(stderr, "\n");
         }
+        std::fprintf(stderr, "gadi batch layout: %d blocks, estimated finish %g s\n", lay.blocks, est);
     }
     const int hist_len = maxit + 2;
     std::vector<Ctl> hc;
     std::vector<unsigned long long> t0, t1;
     float ms = 0.f;
-    if ((s = run_batch(h0, k, smem, units, class_begin, order, lay, max_n, prec, hist_len, st, hc, t0, t1, &ms)) !=
-        GADI_OK)
+    if ((s = run_batch(h0, k, smem, units, class_begin, order, lay, max_n, prec, hist_len, st, hc, t0, t1, &ms,
+                       nr)) != GADI_OK)
         return s;
     gadi_status worst = GADI_OK;
-    for (int u = 0; u < nunits; u++) {
-        const Ctl &c = hc[u];
+    // (system, right-hand side) q = s * nrhs + j: its unit and control block
+    for (int q = 0; q < nsys * nrhs; q++) {
+        const int u = inter ? q / nrhs : q;
+        const Ctl &c = hc[q];
         if (c.status != GADI_OK && worst == GADI_OK) worst = (gadi_status)c.status;
         if (per_unit) {
-            gadi_stats &S = per_unit[u];
+            gadi_stats &S = per_unit[q];
             S.outer_its = c.outer_its;
             S.inner_its_h = c.inner_h;
             S.inner_its_s = c.inner_s;
@@ -1674,7 +1753,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.seconds = (double)(t1[u] - t0[u]) * 1e-9;
             S.status = c.status;
             S.blocks = c.pad; // the size of the group that ran the unit
-            S.alpha = alpha[u / nrhs];
+            S.alpha = alpha[q / nrhs];
             S.restarts = 0;
             S.h_resident = 0;
             S.s_resident = 0;

@@ -25,6 +25,8 @@ size_t kernel_c2d5_smem(int prec, int vec);
 // the batched persistent kernel for the 2D 5-point class
 const void *kernel_batched_2d5(int prec, int vec, size_t *smem, int dd = 0);
 const void *kernel_batched_2d5_dd(int prec, int vec, size_t *smem);
+// the batched kernel with units of four interleaved right-hand sides (FP32)
+const void *kernel_batched4_2d5(size_t *smem);
 // record a message for gadi_last_error() on this thread
 void record_error(const char *msg);
 } // namespace gadi

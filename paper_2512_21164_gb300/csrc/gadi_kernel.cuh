@@ -33,6 +33,16 @@ constexpr int kThreads = GADI_THREADS;
 #ifndef GADI_SMEM_SWEEP
 #define GADI_SMEM_SWEEP 0
 #endif
+// 1: 3D inner phases stage planes of a tile through shared memory
+// (march3_smem); 0: the register-ring march
+#ifndef GADI_SMEM3
+#define GADI_SMEM3 1
+#endif
+// 1: 3D BF16 and FP64 form the CG / CGNR direction in a pointwise pass of
+// its own; 0: inside the stencil pass (as FP32 always does)
+#ifndef GADI_SPLIT_P3
+#define GADI_SPLIT_P3 1
+#endif
 
 // ---------------------------------------------------------------------------
 // arithmetic policies
@@ -283,8 +293,8 @@ __device__ __forceinline__ void load_slot(const Ph &ph, Slot<Ph, W, K, D3> &sl, 
     }
 }
 
-template <int W, int K, bool D3, int PD, class Ph, class AT>
-__device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2], VGrid vg)
+template <int W, int K, bool D3, int PD, class Ph, class ACC>
+__device__ __forceinline__ void march(const Ph &ph, int ne, int ny, int nz, ACC &acc, VGrid vg)
 {
     using FT = typename Ph::Fld::FT;
     using SL = Slot<Ph, W, K, D3>;
@@ -531,6 +541,203 @@ __device__ __forceinline__ void march_smem(const Ph &ph, int ne, int ny, AT (&ac
         }
         cp_async_wait<0>();
         __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the shared-memory-staged 3D sweep (16-byte rows per lane)
+// ---------------------------------------------------------------------------
+// The block's warps take the NWB consecutive y rows of one tile of a strip
+// (as in march) and march z together, one plane of the tile per step.  Each
+// step's inputs reach the SM by asynchronous 16-byte copies issued SM3_PD
+// planes ahead into a block-wide ring of plane slots: per field vector the
+// tile's rows plus the row below and above it (copied by the first and last
+// warp), the x-halo chunks of each row (lanes 0 / 31), and the own-point
+// vectors of each row.  A warp reads its y neighbours from the rows its
+// neighbour warps copied, so every row crosses from memory to the SM once per
+// phase, and the loads in flight cost shared memory instead of registers.
+// One block barrier per step makes a plane's copies visible to every warp
+// and frees the slot of the plane before it.  Outside the grid the copies
+// zero-fill (Dirichlet).
+constexpr int SM3_NWB = kThreads / 32;           // rows of a tile
+#ifndef GADI_SM3_PD
+#define GADI_SM3_PD 3
+#endif
+constexpr int SM3_PD = GADI_SM3_PD;              // planes copied ahead
+constexpr int SM3_NS = SM3_PD + 1;               // plane slots
+template <int NF, int NO>
+struct Sm3Layout {
+    static constexpr int ROW = 32 * 16;                              // a row's lane chunks
+    static constexpr int FIELD = NF * (SM3_NWB + 2) * ROW;           // field rows
+    static constexpr int HALO = NF * SM3_NWB * 2 * 16;               // x-halo chunks
+    static constexpr int SLOT = FIELD + HALO + NO * SM3_NWB * ROW;   // + own rows
+    // field vector k, tile row j (0: the row below the tile, NWB + 1: above)
+    static constexpr int field(int k, int j) { return (k * (SM3_NWB + 2) + j) * ROW; }
+    // x-halo chunk of field vector k at tile row w (0-based), side 0 left / 1 right
+    static constexpr int halo(int k, int w, int side) { return FIELD + ((k * SM3_NWB + w) * 2 + side) * 16; }
+    static constexpr int own(int k, int w) { return FIELD + HALO + (k * SM3_NWB + w) * ROW; }
+};
+// the largest slot of the inner phases: one field vector and three own-point
+// vectors (CGNR's S2), above two field vectors and none (the fused direction)
+constexpr int SM3_SLOT_MAX = Sm3Layout<1, 3>::SLOT > Sm3Layout<2, 0>::SLOT ? Sm3Layout<1, 3>::SLOT
+                                                                           : Sm3Layout<2, 0>::SLOT;
+constexpr int SM3_BYTES = SM3_NS * SM3_SLOT_MAX;
+
+// copy plane p of the tile (rows yy0 - 1 .. yy0 + NWB) into a slot
+template <int W, class Ph>
+__device__ __forceinline__ void sm3_issue_plane(const Ph &ph, unsigned char *slot, int p, bool own, int nz,
+                                                int ny, int ne, int yy0, int e0, int lane, int wib)
+{
+    using F = typename Ph::Fld;
+    using S = typename F::S;
+    using L = Sm3Layout<F::NF, Ph::NO>;
+    const bool act = e0 < ne;
+    const bool pin = p >= 0 && p < nz;
+    const int yy = yy0 + wib;
+    const long long g = ((long long)p * ny + yy) * ne + e0; // this warp's row
+    const bool rin = pin && act && yy < ny;
+#pragma unroll
+    for (int k = 0; k < F::NF; k++) {
+        if (!ph.f.used(k)) continue;
+        const S *base = ph.f.vec(k);
+        cp_async16(slot + L::field(k, wib + 1) + lane * 16, rin ? (const void *)(base + g) : (const void *)base, rin);
+        if (lane == 0) {
+            const bool ok = rin && e0 > 0;
+            cp_async16(slot + L::halo(k, wib, 0), ok ? (const void *)(base + g - W) : (const void *)base, ok);
+        }
+        if (lane == 31) {
+            const bool ok = rin && e0 + W < ne;
+            cp_async16(slot + L::halo(k, wib, 1), ok ? (const void *)(base + g + W) : (const void *)base, ok);
+        }
+        if (wib == 0) { // the row below the tile
+            const bool ok = pin && act && yy0 > 0;
+            cp_async16(slot + L::field(k, 0) + lane * 16, ok ? (const void *)(base + g - ne) : (const void *)base,
+                       ok);
+        }
+        if (wib == SM3_NWB - 1) { // the row above the tile
+            const bool ok = pin && act && yy + 1 < ny;
+            cp_async16(slot + L::field(k, SM3_NWB + 1) + lane * 16,
+                       ok ? (const void *)(base + g + ne) : (const void *)base, ok);
+        }
+    }
+    if (own) {
+#pragma unroll
+        for (int k = 0; k < Ph::NO; k++) {
+            if (!ph.own_used(k)) continue;
+            const S *base = ph.own_vec(k);
+            cp_async16(slot + L::own(k, wib) + lane * 16, rin ? (const void *)(base + g) : (const void *)base, rin);
+        }
+    }
+}
+
+template <int W, int K, class Ph, class AT>
+__device__ __forceinline__ void march3_smem(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2], unsigned char *sm,
+                                            VGrid vg)
+{
+    using F = typename Ph::Fld;
+    using S = typename F::S;
+    using FT = typename F::FT;
+    using L = Sm3Layout<F::NF, Ph::NO>;
+    static_assert(W * sizeof(S) == 16, "march3_smem needs 16-byte lane chunks");
+    static_assert(K == 1, "the 3D class has one x neighbour per side");
+    static_assert(L::SLOT <= SM3_SLOT_MAX, "slot layout");
+    static_assert(SM3_PD >= 2, "the wait below keeps planes m+2.. in flight");
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nstrips = (ne + 32 * W - 1) / (32 * W);
+    const int nyt = (ny + SM3_NWB - 1) / SM3_NWB;
+    const int ncols = nstrips * nyt;
+    // the block's contiguous share of the (strip, y-tile, z) units: the same
+    // for all its warps, so every warp takes every step and every barrier
+    int u, u1;
+    {
+        const int nb = vg.n, bi = vg.b, nu = ncols * nz;
+        const int q = nu / nb, rem = nu - q * nb;
+        u = bi * q + min(bi, rem);
+        u1 = u + q + (bi < rem ? 1 : 0);
+    }
+    while (u < u1) {
+        const int col = u / nz;
+        const int m0 = u - col * nz;
+        const int m1 = min(nz, m0 + (u1 - u));
+        u += m1 - m0;
+        const int strip = col / nyt;
+        const int yy0 = (col - strip * nyt) * SM3_NWB;
+        const int yy = yy0 + wib;
+        const int e0 = strip * 32 * W + lane * W;
+        const bool act = e0 < ne && yy < ny;
+        const long long cbase = (long long)yy * ne + e0;
+        const long long mstride = (long long)ne * ny;
+        auto slot_of = [&](int p) { return sm + ((unsigned)(p - m0) % SM3_NS) * SM3_SLOT_MAX; };
+        // plane m0 - 1 of this warp's row: loaded directly (only its centre
+        // values are used)
+        typename F::template Raw<W> raw{};
+        if (act && m0 > 0) ph.f.template load<W>(cbase + (long long)(m0 - 1) * mstride, raw);
+        FT dn[W], cu[W], up[W];
+        ph.f.template value<W>(raw, dn);
+        for (int p = m0; p < m0 + SM3_PD; ++p) {
+            if (p <= m1) sm3_issue_plane<W>(ph, slot_of(p), p, p < m1, nz, ny, ne, yy0, e0, lane, wib);
+            cp_async_commit();
+        }
+        for (int m = m0; m < m1; ++m) {
+            cp_async_wait<SM3_PD - 2>(); // planes <= m + 1 of this thread have landed
+            __syncthreads();             // ... of every thread; every warp is past step m - 1
+            {
+                const int p = m + SM3_PD; // into the slot of plane m - 1
+                if (p <= m1) sm3_issue_plane<W>(ph, slot_of(p), p, p < m1, nz, ny, ne, yy0, e0, lane, wib);
+                cp_async_commit();
+            }
+            const unsigned char *sc = slot_of(m), *su = slot_of(m + 1);
+            auto row = [&](const unsigned char *sl, int j, int k) {
+                return (const S *)(sl + L::field(k, j) + lane * 16);
+            };
+            if (m == m0) {
+                ph.f.template from_smem<W>(row(sc, wib + 1, 0), row(sc, wib + 1, F::NF - 1), raw);
+                ph.f.template value<W>(raw, cu);
+            }
+            ph.f.template from_smem<W>(row(su, wib + 1, 0), row(su, wib + 1, F::NF - 1), raw);
+            ph.f.template value<W>(raw, up);
+            FT lh[K], rh[K];
+            lh[0] = __shfl_up_sync(0xffffffffu, cu[W - 1], 1);
+            rh[0] = __shfl_down_sync(0xffffffffu, cu[0], 1);
+            if (lane == 0) {
+                typename F::template Raw<K> rk;
+                ph.f.template from_smem<K>((const S *)(sc + L::halo(0, wib, 0)) + (W - K),
+                                           (const S *)(sc + L::halo(F::NF - 1, wib, 0)) + (W - K), rk);
+                ph.f.template value<K>(rk, lh);
+            }
+            if (lane == 31) {
+                typename F::template Raw<K> rk;
+                ph.f.template from_smem<K>((const S *)(sc + L::halo(0, wib, 1)),
+                                           (const S *)(sc + L::halo(F::NF - 1, wib, 1)), rk);
+                ph.f.template value<K>(rk, rh);
+            }
+            FT w[W], e[W];
+#pragma unroll
+            for (int v = 0; v < W; v++) {
+                w[v] = (v >= K) ? cu[v - K] : lh[v];
+                e[v] = (v + K < W) ? cu[v + K] : rh[v + K - W];
+            }
+            if (act) {
+                FT sy[W], ny_[W];
+                ph.f.template from_smem<W>(row(sc, wib, 0), row(sc, wib, F::NF - 1), raw);
+                ph.f.template value<W>(raw, sy);
+                ph.f.template from_smem<W>(row(sc, wib + 2, 0), row(sc, wib + 2, F::NF - 1), raw);
+                ph.f.template value<W>(raw, ny_);
+                typename Ph::Own o;
+                const S *oc[Ph::NO > 0 ? Ph::NO : 1];
+#pragma unroll
+                for (int k = 0; k < Ph::NO; k++) oc[k] = (const S *)(sc + L::own(k, wib) + lane * 16);
+                ph.own_from_smem(oc, o);
+                ph.out(cbase + (long long)m * mstride, o, cu, w, e, sy, ny_, dn, up, acc);
+            }
+#pragma unroll
+            for (int v = 0; v < W; v++) {
+                dn[v] = cu[v];
+                cu[v] = up[v];
+            }
+        }
+        cp_async_wait<0>();
+        __syncthreads(); // every warp is done with the slots before the next column reuses them
     }
 }
 
@@ -990,7 +1197,9 @@ struct StencilImpl {
     static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead (register ring)
     // 2D rows with 16-byte lane chunks go through the shared-memory-staged sweep
     static constexpr bool USE_SMEM = GADI_SMEM_SWEEP && !D3 && (WI * sizeof(S) == 16);
-    static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : 0; // dynamic shared bytes
+    // 3D rows with 16-byte lane chunks: the block-wide plane ring (march3_smem)
+    static constexpr bool USE_SMEM3 = GADI_SMEM3 && D3 && (WI * sizeof(S) == 16);
+    static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : (USE_SMEM3 ? SM3_BYTES : 0);
     const Params &P;
     VGrid vg;
     int ne, ny, nz;
@@ -1021,6 +1230,11 @@ struct StencilImpl {
         for (int k = 0; k < 6; k++) ca.c[k] = p.co.a_c[k];
     }
 
+    __device__ static unsigned char *block_smem()
+    {
+        extern __shared__ __align__(16) unsigned char gadi_dsmem[];
+        return gadi_dsmem;
+    }
     __device__ static unsigned char *warp_smem()
     {
         extern __shared__ __align__(16) unsigned char gadi_dsmem[];
@@ -1032,6 +1246,7 @@ struct StencilImpl {
     {
         acc[0] = acc[1] = AT(0);
         if constexpr (USE_SMEM) march_smem<WI, K>(ph, ne, ny, acc, warp_smem(), vg);
+        else if constexpr (USE_SMEM3) march3_smem<WI, K>(ph, ne, ny, nz, acc, block_smem(), vg);
         else march<WI, K, D3, PD>(ph, ne, ny, nz, acc, vg);
     }
 
@@ -1111,7 +1326,7 @@ struct StencilImpl {
     // Measured at 512^3 / 320^3: 5-6 % faster per outer iteration for BF16
     // and FP64, slower for FP32 (whose fused pass recomputes p at the
     // neighbour rows more cheaply than an extra pass over memory costs).
-    static constexpr bool SPLIT_P = D3 && (PREC == P_BF16 || PREC == P_FP64);
+    static constexpr bool SPLIT_P = GADI_SPLIT_P3 && D3 && (PREC == P_BF16 || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
         using A2 = typename InnerAr<PREC>::T;

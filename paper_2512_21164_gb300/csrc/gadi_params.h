@@ -91,6 +91,10 @@ struct Params {
     // sig_a: the sign T carries in the FP64 set `a` (A, N: +1, A^T: -1, M: 0)
     const double *sig;
     double sig_a;
+    // a batched unit of four interleaved right-hand sides: the iterate (two
+    // ping-pong buffers) and the right-hand sides as [n][4] FP64 work
+    // vectors; x and b above are then the caller's [4][n] arrays
+    double *xm0, *xm1, *bm;
     double *part;  // 2 slots x 2 values x gridDim doubles
     double *hist;  // maxit + 1 doubles (device)
     Ctl *ctl;

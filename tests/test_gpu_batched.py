@@ -116,3 +116,54 @@ def test_batched_double_fp64_residual_matches_single(prec):
             assert abs(u["outer_its"] - s1["outer_its"]) <= max(2, BAND[prec] * s1["outer_its"])
     for h in handles:
         h.close()
+
+
+@pytest.mark.parametrize("interleave", [1, 0])
+@pytest.mark.parametrize("group", [0, 3])
+def test_batched_four_rhs_interleaved_matches_oracle(interleave, group):
+    """Four right-hand sides per system, FP32 inner solves: interleaved as
+    [n][4] in one unit (each right-hand side with its own scalars, stopping
+    and outer iteration) or one unit each -- every right-hand side must reach
+    the oracle's outcome for it, within the outer-iteration band.  One system
+    gets a right-hand side of zeros (solved at x_0 = 0) and one a right-hand
+    side of another shape and scale, so the units run with some right-hand
+    sides frozen while others go on."""
+    import torch
+    nrhs = 4
+    systems = _systems()
+    g = SplitMix64(78)
+    handles, bs, xs, alphas, rhs = [], [], [], [], []
+    for si, (p, a) in enumerate(systems):
+        orc = O.Oracle(p)
+        cols = [orc.rhs(g.uniform_array(p.nvec)) for _ in range(nrhs)]
+        if si == 0:
+            cols[2] = np.zeros(p.nvec)
+        if si == 1:
+            cols[1] = cols[1] * 1e3 + orc.rhs(np.sin(np.arange(p.nvec) * 0.7))
+        bb = np.concatenate(cols)
+        rhs.append(bb)
+        handles.append(G.Gadi.from_problem(p))
+        bs.append(dev64(bb))
+        xs.append(torch.zeros(nrhs * p.nvec, dtype=torch.float64, device="cuda"))
+        alphas.append(a)
+    st, stats = G.solve_batched(handles, nrhs, bs, xs, alphas, 1.0, FP32, 1e-10, 3000, tol_h=1e-3, tol_s=1e-3,
+                                batch_group=group, batch_interleave=interleave)
+    assert st == G.OK, G.status_str(st)
+    for s, (p, a) in enumerate(systems):
+        orc = O.Oracle(p)
+        xg_all = xs[s].cpu().numpy()
+        for j in range(nrhs):
+            b = rhs[s][j * p.nvec:(j + 1) * p.nvec]
+            xg = xg_all[j * p.nvec:(j + 1) * p.nvec]
+            u = stats[s * nrhs + j]
+            _, so = orc.gadi(b, a, 1.0, FP32, tol=1e-10, maxit=3000, tol_h=1e-3, tol_s=1e-3)
+            assert so["status"] == "OK" and u["status"] == G.OK, (s, j, so["status"], u["status"])
+            assert abs(u["outer_its"] - so["outer_its"]) <= max(2, BAND[FP32] * so["outer_its"]), \
+                (s, j, u["outer_its"], so["outer_its"])
+            if not np.any(b):
+                assert u["outer_its"] == 0 and not np.any(xg)
+                continue
+            rel = np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b)
+            assert rel <= 1e-10, (s, j, rel)
+    for h in handles:
+        h.close()

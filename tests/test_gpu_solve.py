@@ -439,6 +439,37 @@ def test_headline_geometry_solve_matches_oracle():
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+@pytest.mark.parametrize("blocks", [4, 0])
+def test_3d_plane_ring_solve_matches_oracle(prec, blocks):
+    """The 3D inner phases with 16-byte rows march a block's tile of y rows
+    through z together, staging planes in shared memory.  On 24 x 40 x 64
+    (three y-tiles, the last one partial, one partial strip) with 4 blocks
+    every block marches 48 planes and crosses from one column to the next;
+    with the default grid (one block per SM) most blocks take one to two
+    planes.  Against the oracle: outer iterations within the band, relres
+    <= 1e-10 by the oracle's residual, forward error within 10x."""
+    from workloads import K_3D7, Problem, SplitMix64
+    p = Problem(K_3D7, 24, 40, 64, 1.0 / 25, (10.0, 20.0, 30.0))
+    xt = SplitMix64(219).uniform_array(p.nvec)
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    a = 2 * alpha_star(p)
+    th, ts = _tols(prec)
+    xo, so = orc.gadi(b, a, 1.0, prec, tol=1e-10, maxit=3000, tol_h=th, tol_s=ts, s_pointwise=True)
+    kw = dict(max_blocks=blocks) if blocks else {}
+    st, sg, xg, hg = _gpu_solve(p, b, a, 1.0, prec, 1e-10, 3000, **kw)
+    assert so["status"] == "OK" and st == G.OK, G.status_str(st)
+    if blocks:
+        assert sg["blocks"] == blocks
+    assert abs(sg["outer_its"] - so["outer_its"]) <= max(2, BAND[prec] * so["outer_its"]), \
+        (sg["outer_its"], so["outer_its"])
+    assert np.linalg.norm(b - orc.apply(O.OP_A, xg)) / np.linalg.norm(b) <= 1e-10
+    fe_g = np.linalg.norm(xg - xt) / np.linalg.norm(xt)
+    fe_o = np.linalg.norm(xo - xt) / np.linalg.norm(xt)
+    assert fe_g <= 10 * fe_o + 1e-14, (fe_g, fe_o)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
 def test_backward_err_stat_matches_oracle(prec):
     """gadi_stats.backward_err (opt-in) is eq. (3.2) of the returned x, host
     and device vectors alike; off by default (-1)."""

@@ -70,6 +70,11 @@ H_CASES = {
     "2d_narrow_tall": lambda: Problem(K_2D5, 8, 400, 1, 1.0 / 9, (30.0, 50.0, 0.0)),
     "3d_vec": lambda: Problem(K_3D7, 16, 16, 16, 1.0 / 17, (10.0, 10.0, 10.0)),
     "3d_ragged": lambda: Problem(K_3D7, 7, 5, 9, 1.0 / 8, (13.0, 29.0, 41.0)),
+    # 16-byte rows in every precision: the plane-ring sweep with a partial
+    # last y-tile (40 = 16 + 16 + 8 rows) and a partial strip, z runs that
+    # cross from one column to the next; and rows of two strips
+    "3d_tiles": lambda: Problem(K_3D7, 24, 40, 200, 1.0 / 25, (10.0, 20.0, 30.0)),
+    "3d_strips": lambda: Problem(K_3D7, 136, 17, 30, 1.0 / 137, (10.0, 20.0, 30.0)),
     "cplx_vec": lambda: Problem(K_C2D5, 32, 32, 1, 1.0 / 33, (0.0, 0.0, 0.0), 2.0, 40.0),
     "csr": lambda: _dyadic_csr(500, 9),
 }
@@ -79,6 +84,8 @@ S_CASES = {
     "2d_ragged": lambda: Problem(K_2D5, 37, 5, 1, 0.125, (8.0, 8.0, 0.0)),
     "2d_tall": lambda: Problem(K_2D5, 64, 700, 1, 0.125, (8.0, 8.0, 0.0)),
     "3d_vec": lambda: Problem(K_3D7, 16, 16, 16, 0.125, (8.0, 8.0, 8.0)),
+    "3d_tiles": lambda: Problem(K_3D7, 24, 40, 200, 0.125, (8.0, 8.0, 8.0)),
+    "3d_strips": lambda: Problem(K_3D7, 136, 17, 30, 0.125, (8.0, 8.0, 8.0)),
     "csr": lambda: _dyadic_csr(500, 11),
 }
 
@@ -166,6 +173,8 @@ RAND_CASES = {
     "2d_tall": lambda: conv_diff_2d(64, 112, ny=700),
     "2d_wide_tall": lambda: conv_diff_2d(2560, 117, ny=200),
     "3d_vec": lambda: conv_diff_3d(16, 106),
+    "3d_tiles": lambda: (Problem(K_3D7, 24, 40, 200, 1.0 / 25, (10.0, 20.0, 30.0)),
+                         SplitMix64(118).uniform_array(24 * 40 * 200)),
 }
 
 
@@ -206,7 +215,7 @@ def _abs_n(p, v):
     return out.ravel()
 
 
-@pytest.mark.parametrize("case", ["2d_vec", "2d_tall", "3d_vec"])
+@pytest.mark.parametrize("case", ["2d_vec", "2d_tall", "3d_vec", "3d_tiles"])
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_solve_s_one_step_elementwise_random(case, prec):
     p, xt = RAND_CASES[case]()
