@@ -38,11 +38,7 @@ constexpr int kThreads = GADI_THREADS;
 #ifndef GADI_SMEM3
 #define GADI_SMEM3 1
 #endif
-// 1: 3D BF16 and FP64 form the CG / CGNR direction in a pointwise pass of
-// its own; 0: inside the stencil pass (as FP32 always does)
-#ifndef GADI_SPLIT_P3
-#define GADI_SPLIT_P3 1
-#endif
+
 
 // ---------------------------------------------------------------------------
 // arithmetic policies
@@ -561,7 +557,7 @@ __device__ __forceinline__ void march_smem(const Ph &ph, int ne, int ny, AT (&ac
 // zero-fill (Dirichlet).
 constexpr int SM3_NWB = kThreads / 32;           // rows of a tile
 #ifndef GADI_SM3_PD
-#define GADI_SM3_PD 3
+#define GADI_SM3_PD 4
 #endif
 constexpr int SM3_PD = GADI_SM3_PD;              // planes copied ahead
 constexpr int SM3_NS = SM3_PD + 1;               // plane slots
@@ -631,9 +627,10 @@ __device__ __forceinline__ void sm3_issue_plane(const Ph &ph, unsigned char *slo
 }
 
 template <int W, int K, class Ph, class AT>
-__device__ __forceinline__ void march3_smem(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2], unsigned char *sm,
-                                            VGrid vg)
+__device__ __forceinline__ void march3_smem(const Ph &ph, int ne, int ny, int nz, AT (&acc)[2], VGrid vg)
 {
+    extern __shared__ __align__(16) unsigned char gadi_dsmem[];
+    unsigned char *const sm = gadi_dsmem;
     using F = typename Ph::Fld;
     using S = typename F::S;
     using FT = typename F::FT;
@@ -1197,8 +1194,16 @@ struct StencilImpl {
     static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead (register ring)
     // 2D rows with 16-byte lane chunks go through the shared-memory-staged sweep
     static constexpr bool USE_SMEM = GADI_SMEM_SWEEP && !D3 && (WI * sizeof(S) == 16);
-    // 3D rows with 16-byte lane chunks: the block-wide plane ring (march3_smem)
-    static constexpr bool USE_SMEM3 = GADI_SMEM3 && D3 && (WI * sizeof(S) == 16);
+    // 3D FP32 rows with 16-byte lane chunks: the block-wide plane ring
+    // (march3_smem).  At 512^3 it took a CG iteration on H from 1.07 to
+    // 0.77 ms and the first 300 outer iterations of the solve from 19.4 to
+    // 16.0 ms each.  BF16 and FP64 keep the register ring: with the plane
+    // ring a BF16 CG iteration took 0.52 instead of 0.59 ms, but the solve
+    // (few inner iterations per outer one, its FP64 residual step slower in
+    // the kernel that also holds the plane ring) 10.0 instead of 8.1 ms per
+    // outer iteration; FP64 inner solves, bound by the FP64 pipe, ran 7 %
+    // slower per CG iteration.
+    static constexpr bool USE_SMEM3 = GADI_SMEM3 && D3 && PREC == P_FP32 && (WI * sizeof(S) == 16);
     static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : (USE_SMEM3 ? SM3_BYTES : 0);
     const Params &P;
     VGrid vg;
@@ -1230,11 +1235,6 @@ struct StencilImpl {
         for (int k = 0; k < 6; k++) ca.c[k] = p.co.a_c[k];
     }
 
-    __device__ static unsigned char *block_smem()
-    {
-        extern __shared__ __align__(16) unsigned char gadi_dsmem[];
-        return gadi_dsmem;
-    }
     __device__ static unsigned char *warp_smem()
     {
         extern __shared__ __align__(16) unsigned char gadi_dsmem[];
@@ -1246,7 +1246,7 @@ struct StencilImpl {
     {
         acc[0] = acc[1] = AT(0);
         if constexpr (USE_SMEM) march_smem<WI, K>(ph, ne, ny, acc, warp_smem(), vg);
-        else if constexpr (USE_SMEM3) march3_smem<WI, K>(ph, ne, ny, nz, acc, block_smem(), vg);
+        else if constexpr (USE_SMEM3) march3_smem<WI, K>(ph, ne, ny, nz, acc, vg);
         else march<WI, K, D3, PD>(ph, ne, ny, nz, acc, vg);
     }
 
@@ -1320,13 +1320,14 @@ struct StencilImpl {
         ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs; ph.sig = P.sig;
         sweep(ph, acc);
     }
-    // 3D BF16 and FP64: the direction update p = fl_s(src + beta p_old) (p =
-    // src at first) as its own pointwise pass (src = P.r: the CG residual r
-    // or the CGNR residual t), then the stencil pass on the stored p.
-    // Measured at 512^3 / 320^3: 5-6 % faster per outer iteration for BF16
-    // and FP64, slower for FP32 (whose fused pass recomputes p at the
-    // neighbour rows more cheaply than an extra pass over memory costs).
-    static constexpr bool SPLIT_P = GADI_SPLIT_P3 && D3 && (PREC == P_BF16 || PREC == P_FP64);
+    // 3D BF16 and FP64 (the register ring): the direction update p =
+    // fl_s(src + beta p_old) (p = src at first) as its own pointwise pass
+    // (src = P.r: the CG residual r or the CGNR residual t), then the stencil
+    // pass on the stored p.  Measured at 512^3 / 320^3: 5-6 % faster per
+    // outer iteration for BF16 and FP64, slower for FP32 (whose fused pass
+    // recomputes p at the neighbour rows more cheaply than an extra pass over
+    // memory costs).
+    static constexpr bool SPLIT_P = D3 && !USE_SMEM3 && (PREC == P_BF16 || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
         using A2 = typename InnerAr<PREC>::T;

@@ -441,8 +441,9 @@ def test_headline_geometry_solve_matches_oracle():
 @pytest.mark.parametrize("prec", [FP64, FP32, BF16])
 @pytest.mark.parametrize("blocks", [4, 0])
 def test_3d_plane_ring_solve_matches_oracle(prec, blocks):
-    """The 3D inner phases with 16-byte rows march a block's tile of y rows
-    through z together, staging planes in shared memory.  On 24 x 40 x 64
+    """The 3D FP32 inner phases with 16-byte rows march a block's tile of y
+    rows through z together, staging planes in shared memory (BF16 and FP64
+    take the register ring on the same shapes).  On 24 x 40 x 64
     (three y-tiles, the last one partial, one partial strip) with 4 blocks
     every block marches 48 planes and crosses from one column to the next;
     with the default grid (one block per SM) most blocks take one to two

@@ -70,9 +70,9 @@ H_CASES = {
     "2d_narrow_tall": lambda: Problem(K_2D5, 8, 400, 1, 1.0 / 9, (30.0, 50.0, 0.0)),
     "3d_vec": lambda: Problem(K_3D7, 16, 16, 16, 1.0 / 17, (10.0, 10.0, 10.0)),
     "3d_ragged": lambda: Problem(K_3D7, 7, 5, 9, 1.0 / 8, (13.0, 29.0, 41.0)),
-    # 16-byte rows in every precision: the plane-ring sweep with a partial
-    # last y-tile (40 = 16 + 16 + 8 rows) and a partial strip, z runs that
-    # cross from one column to the next; and rows of two strips
+    # 16-byte rows in every precision (FP32: the plane-ring sweep) with a
+    # partial last y-tile (40 = 16 + 16 + 8 rows) and a partial strip, z runs
+    # that cross from one column to the next; and rows of two strips
     "3d_tiles": lambda: Problem(K_3D7, 24, 40, 200, 1.0 / 25, (10.0, 20.0, 30.0)),
     "3d_strips": lambda: Problem(K_3D7, 136, 17, 30, 1.0 / 137, (10.0, 20.0, 30.0)),
     "cplx_vec": lambda: Problem(K_C2D5, 32, 32, 1, 1.0 / 33, (0.0, 0.0, 0.0), 2.0, 40.0),
