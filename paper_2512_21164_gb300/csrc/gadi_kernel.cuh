@@ -1194,16 +1194,23 @@ struct StencilImpl {
     static constexpr int PD = D3 ? 1 : 1; // rows prefetched ahead (register ring)
     // 2D rows with 16-byte lane chunks go through the shared-memory-staged sweep
     static constexpr bool USE_SMEM = GADI_SMEM_SWEEP && !D3 && (WI * sizeof(S) == 16);
-    // 3D FP32 rows with 16-byte lane chunks: the block-wide plane ring
-    // (march3_smem).  At 512^3 it took a CG iteration on H from 1.07 to
-    // 0.77 ms and the first 300 outer iterations of the solve from 19.4 to
-    // 16.0 ms each.  BF16 and FP64 keep the register ring: with the plane
-    // ring a BF16 CG iteration took 0.52 instead of 0.59 ms, but the solve
-    // (few inner iterations per outer one, its FP64 residual step slower in
-    // the kernel that also holds the plane ring) 10.0 instead of 8.1 ms per
-    // outer iteration; FP64 inner solves, bound by the FP64 pipe, ran 7 %
-    // slower per CG iteration.
-    static constexpr bool USE_SMEM3 = GADI_SMEM3 && D3 && PREC == P_FP32 && (WI * sizeof(S) == 16);
+    // 3D FP32 and BF16 rows with 16-byte lane chunks: the block-wide plane
+    // ring (march3_smem).  At 512^3 it took a CG iteration on H from 1.07 to
+    // 0.77 ms (FP32) and 0.59 to 0.52 ms (BF16, the direction update fused,
+    // see SPLIT_P), and the first 300 outer iterations of the solve from
+    // 19.4 to 15.1 ms (FP32) and 8.1 to 7.9 ms (BF16) each.  FP64 inner
+    // solves, bound by the FP64 pipe, ran 7 % slower per CG iteration with it
+    // and keep the register ring.
+        static constexpr bool USE_SMEM3 = GADI_SMEM3 && D3 && PREC != P_FP64 && (WI * sizeof(S) == 16);
+    // rows the residual's register ring prefetches: none in the kernels with
+    // the plane ring, whose inner phases otherwise push the kernel's
+    // allocation into spills inside the residual's loop (a BF16 solve then
+    // ran 10.0 instead of 7.9 ms per outer iteration at 512^3, FP32 16.0
+    // instead of 15.1), nor in the 3D FP64 kernel (spills 220 -> 16 bytes,
+    // CGNR iteration 5.87 -> 5.47 ms); the residual is bound by the FP64
+    // pipe, and its step time did not change (4.46 ms FP32, 4.65 ms BF16,
+    // 3.78 ms FP64)
+    static constexpr int RPD = (USE_SMEM3 || (D3 && PREC == P_FP64)) ? 0 : PD;
     static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : (USE_SMEM3 ? SM3_BYTES : 0);
     const Params &P;
     VGrid vg;
@@ -1255,7 +1262,7 @@ struct StencilImpl {
         double a[2] = {0.0, 0.0}; // a[1]: the FP32 partial of the r_s norm in its low 32 bits
         PhResidual<PREC, WR, K, D3, DD> ph{{xin, y}, xout, P.b, P.r_out, (S *)P.r, ca, P.r_lo_out, P.sig, P.sig_a};
         ph.dpow2 = P.ad_pow2;
-        march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
+        march<WR, K, D3, RPD>(ph, ne, ny, nz, a, vg);
         acc[0] = a[0];
         acc[1] = (double)__int_as_float(__double2hiint(a[1])) + (double)__int_as_float(__double2loint(a[1]));
     }
@@ -1264,7 +1271,7 @@ struct StencilImpl {
         PhResidual<PREC, WR, K, D3> ph{{x, nullptr}, yout, nullptr, nullptr, nullptr, ca, nullptr, P.sig, P.sig_a};
         ph.dpow2 = P.ad_pow2;
         double a[2] = {0.0, 0.0};
-        march<WR, K, D3, PD>(ph, ne, ny, nz, a, vg);
+        march<WR, K, D3, RPD>(ph, ne, ny, nz, a, vg);
     }
     __device__ void h1(bool first, C beta, const S *pold, S *pnew, AT (&acc)[2]) const
     {
@@ -1320,13 +1327,14 @@ struct StencilImpl {
         ph.pnew = pnew; ph.u = (S *)P.u; ph.sc = cs; ph.sig = P.sig;
         sweep(ph, acc);
     }
-    // 3D BF16 and FP64 (the register ring): the direction update p =
-    // fl_s(src + beta p_old) (p = src at first) as its own pointwise pass
-    // (src = P.r: the CG residual r or the CGNR residual t), then the stencil
-    // pass on the stored p.  Measured at 512^3 / 320^3: 5-6 % faster per
+    // 3D FP64 (the register ring): the direction update p = fl_s(src + beta
+    // p_old) (p = src at first) as its own pointwise pass (src = P.r: the CG
+    // residual r or the CGNR residual t), then the stencil pass on the stored
+    // p.  Measured at 512^3 / 320^3 on the register ring: 5-6 % faster per
     // outer iteration for BF16 and FP64, slower for FP32 (whose fused pass
     // recomputes p at the neighbour rows more cheaply than an extra pass over
-    // memory costs).
+    // memory costs).  On the plane ring the fused update is faster for BF16
+    // too (CG iteration 0.52 vs 0.56 ms at 512^3).
     static constexpr bool SPLIT_P = D3 && !USE_SMEM3 && (PREC == P_BF16 || PREC == P_FP64);
     __device__ void p_update(bool first, C beta, const S *pold, S *pnew) const
     {
