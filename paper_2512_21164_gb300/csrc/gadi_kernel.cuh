@@ -1206,11 +1206,12 @@ struct StencilImpl {
     // the plane ring, whose inner phases otherwise push the kernel's
     // allocation into spills inside the residual's loop (a BF16 solve then
     // ran 10.0 instead of 7.9 ms per outer iteration at 512^3, FP32 16.0
-    // instead of 15.1), nor in the 3D FP64 kernel (spills 220 -> 16 bytes,
-    // CGNR iteration 5.87 -> 5.47 ms); the residual is bound by the FP64
-    // pipe, and its step time did not change (4.46 ms FP32, 4.65 ms BF16,
-    // 3.78 ms FP64)
-    static constexpr int RPD = (USE_SMEM3 || (D3 && PREC == P_FP64)) ? 0 : PD;
+    // instead of 15.1), in the 3D FP64 kernel (spills 220 -> 16 bytes, CGNR
+    // iteration 5.87 -> 5.47 ms) and in the 2D tensor-memory kernel (CMODE 1;
+    // 2048^2 solve 1.149 -> 1.143 s); the residual is bound by the FP64 pipe,
+    // and its step time did not change (4.46 ms FP32, 4.65 ms BF16, 3.78 ms
+    // FP64 at 512^3)
+    static constexpr int RPD = (USE_SMEM3 || (D3 && PREC == P_FP64) || CMODE == 1) ? 0 : PD;
     static constexpr int DSMEM = USE_SMEM ? (kThreads / 32) * SMEM_WARP : (USE_SMEM3 ? SM3_BYTES : 0);
     const Params &P;
     VGrid vg;
