@@ -791,6 +791,7 @@ def run_batched(args):
             al.append(a)
         maxit = args.maxit5 if not scaled else 20000
         tune_s = None
+        hres = {} if args.hres5 < 0 else {"h_resident": args.hres5}
         if args.group5 <= 0:
             # the group-size tuner runs on the first batch of these grids and
             # alpha values in the process (timed here, outside the measured
@@ -798,12 +799,12 @@ def run_batched(args):
             xw = [torch.zeros_like(v) for v in xs]
             t0 = time.perf_counter()
             G.solve_batched(hs, 4, bs, xw, al, OMEGA, G.FP32, TOL, 2, tol_h=TOL_INNER, tol_s=TOL_INNER,
-                            batch_group=args.group5, batch_interleave=args.interleave5)
+                            batch_group=args.group5, batch_interleave=args.interleave5, **hres)
             tune_s = time.perf_counter() - t0
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record()
-        st, stats = G.solve_batched(hs, 4, bs, xs, al, OMEGA, G.FP32, TOL, maxit, batch_interleave=args.interleave5,
+        st, stats = G.solve_batched(hs, 4, bs, xs, al, OMEGA, G.FP32, TOL, maxit, batch_interleave=args.interleave5, **hres,
                                     tol_h=TOL_INNER,
                                     tol_s=TOL_INNER, batch_group=args.group5)
         ev1.record()
@@ -816,7 +817,8 @@ def run_batched(args):
             "config": {"workload": f"{len(systems)} 2D conv-diff systems N in {{128,256,512,1024}}, 4 rhs each",
                        "alpha": "alpha*(N) x logU[0.5,2]" if scaled else "logU[1e-2,10]", "omega": OMEGA,
                        "maxit": maxit, "u_s": "fp32", "batch_group": args.group5,
-                       "interleaved_rhs": bool(args.interleave5)},
+                       "interleaved_rhs": bool(args.interleave5),
+                       "h_solve": "p in shared memory" if stats[0]["h_resident"] else "streaming"},
             "group_blocks": {f"N={n}": {str(k): int(v) for k, v in zip(*np.unique(
                 [u["blocks"] for i, u in enumerate(stats) if systems[i // 4][0].nx == n], return_counts=True))}
                 for n in sorted({sp.nx for sp, _, _ in systems})},
@@ -963,6 +965,8 @@ def main():
     ap.add_argument("--nsys5", type=int, default=96)
     ap.add_argument("--interleave5", type=int, default=0, help="c5: 1 = the four right-hand sides of a system in one unit")
     ap.add_argument("--group5", type=int, default=0, help="c5: blocks per group (0 = the library's tuner)")
+    ap.add_argument("--hres5", type=int, default=-1,
+                    help="c5: 0 = units take the streaming H-solve (default: the library's, p in shared memory)")
     ap.add_argument("--record-traffic", nargs=2, metavar=("NCU_REPORT", "PROFILE_CASE_LOG"), default=None,
                     help="write the committed traffic record from an ncu report of --profile-case")
     args = ap.parse_args()

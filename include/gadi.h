@@ -158,7 +158,13 @@ typedef struct {
                               stream p through global memory.  Same
                               arithmetic in all three; 1 and 2 give the
                               same bits, 0 differs in the order of the
-                              grid-wide sums.  Other values: INVALID.       */
+                              grid-wide sums.  gadi_solve_batched: >= 1 =
+                              units keep p in shared memory on their
+                              group's blocks (as 1) where every system
+                              admits it (an FP64 residual, 16-byte rows,
+                              a candidate group size whose row share
+                              fits); 0 = streaming.  Other values:
+                              INVALID.                                    */
     gadi_prec u_r;         /* residual precision u_r (Sec. 3.1, u_r <= u):
                               GADI_FP64 or GADI_FP64X2; every problem
                               class, single and batched solves             */
@@ -263,9 +269,11 @@ gadi_status gadi_solve(gadi_handle *h, const double *b, double *x, double alpha,
  * per outer iteration x the grid's side), then moves one class at a time to
  * the size that most lowers the estimated finish time of the batch.  Each
  * group takes units from its class's device-side queue, then from the
- * queues of classes of smaller systems (never a larger one).  A unit is one
+ * queues of classes of smaller systems (never a larger one, nor one whose
+ * rows do not split over the group for the resident H-solve).  A unit is one
  * (system, rhs), or with opts->batch_interleave one system's four right-hand
- * sides.  per_unit (nullable) gets
+ * sides; with opts->h_resident >= 1 (FP32 / BF16, see there) the units' CG on
+ * H keeps p in shared memory.  per_unit (nullable) gets
  * nsys*nrhs entries in the order s*nrhs + j, with `seconds` the unit's own
  * device time and `blocks` the size of the group that ran it.  Returns
  * GADI_OK if every unit converged, else the first non-OK unit status;

@@ -13,6 +13,17 @@ const void *kernel_batched4_2d5(size_t *smem)
     return (const void *)gadi_batched4_kernel;
 }
 
+const void *kernel_batched_2d5_res(int prec)
+{
+    switch (prec) {
+    case P_FP32:
+        return (const void *)gadi_batched_kernel<K_2D5, P_FP32, 4, 2, false, 1>;
+    case P_BF16:
+        return (const void *)gadi_batched_kernel<K_2D5, P_BF16, 8, 2, false, 1>;
+    }
+    return nullptr;
+}
+
 const void *kernel_batched_2d5(int prec, int vec, size_t *smem, int dd)
 {
     if (dd) return kernel_batched_2d5_dd(prec, vec, smem);

@@ -3,17 +3,22 @@
 // group takes (system, right-hand side) units from a device-side queue and runs
 // Algorithm 1 on it with the same phases as a single solve (on the group's
 // blocks, with the group's own barrier, partial sums and work vectors).  Units
-// are queued largest first so the groups finish close together.
+// are queued largest first so the groups finish close together.  RES = 1: the
+// units' CG on H keeps its direction p in shared memory (the SM-resident
+// H-solve of the single solve, on the group's blocks: block b of a group of G
+// owns rows [b ny / G, (b+1) ny / G) of the unit), the launch's dynamic shared
+// memory sized by the host for the largest share a group may take.
 #pragma once
 #include "gadi_params.h"
 #include "gadi_solver.cuh"
 
 namespace gadi {
 
-template <int KIND, int PREC, int WI, int WR, bool DD = false>
+template <int KIND, int PREC, int WI, int WR, bool DD = false, int RES = 0>
 __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel(const __grid_constant__ BatchParams B)
 {
     using SI = StencilImpl<KIND, PREC, WI, WR, DD>;
+    using Ad = StencilAdapter<SI, RES>;
     const int g = B.block_group[blockIdx.x];
     const int gsize = B.group_size[g];
     const VGrid vg{(int)blockIdx.x - B.group_first[g], gsize};
@@ -28,10 +33,12 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
         if (leader) {
             // the group's own class first, then the classes of smaller
             // systems (classes are sorted by system size, largest first): a
-            // group never takes a unit larger than those it was sized for
+            // group never takes a unit larger than those it was sized for,
+            // nor one of a class whose size limits exclude the group's size
             int u = B.nunits;
             for (int k = own_class; k < B.nclasses && u == B.nunits; k++) {
                 const int c = k;
+                if (gsize < B.class_gmin[c] || gsize > B.class_gmax[c]) continue;
                 const int n_c = B.class_begin[c + 1] - B.class_begin[c];
                 if (ld_volatile_int(B.queue + (size_t)c * 32) >= n_c) continue;
                 const int i = atomicAdd(B.queue + (size_t)c * 32, 1);
@@ -63,10 +70,8 @@ __global__ void __launch_bounds__(kThreads, GADI_MIN_BLOCKS) gadi_batched_kernel
         if (u >= B.nunits) return;
         const Params &P = B.units[u];
         {
-            // (units take the streaming H-solve: the resident forms size
-            // their shared memory for one system per launch)
-            StencilAdapter<SI> I(P, vg);
-            Runner<PREC, StencilAdapter<SI>> R(P, I);
+            Ad I(P, vg);
+            Runner<PREC, Ad> R(P, I);
             R.run();
         }
         if (!gs.sync()) return;

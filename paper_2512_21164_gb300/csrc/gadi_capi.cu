@@ -1280,7 +1280,7 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
                       const std::vector<int> &class_begin, const std::vector<int> &order, const BatchLayout &lay,
                       long long max_n, int prec, int hist_len, cudaStream_t st, std::vector<Ctl> &ctl,
                       std::vector<unsigned long long> &t0, std::vector<unsigned long long> &t1, float *timed_ms,
-                      int nr = 1)
+                      int nr = 1, const std::vector<int> *gmin = nullptr, const std::vector<int> *gmax = nullptr)
 {
     // nr = 4: units of four interleaved right-hand sides (gadi_batched4_kernel):
     // 4x the vectors, a third FP64 work vector, 4 control blocks and 4
@@ -1296,8 +1296,8 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
     const size_t nctl = (size_t)nunits * nr;
     // one table buffer: block_group, group_first, group_size, group_class,
     // class_begin, order, queues (32 ints a class), group_unit (32 a group)
-    const size_t nint = (size_t)lay.blocks + 3 * (size_t)ngroups + (nclasses + 1) + nunits + 32 * (size_t)nclasses +
-                        32 * (size_t)ngroups;
+    const size_t nint = (size_t)lay.blocks + 3 * (size_t)ngroups + (nclasses + 1) + 2 * (size_t)nclasses + nunits +
+                        32 * (size_t)nclasses + 32 * (size_t)ngroups;
     std::vector<int> tab(nint, 0);
     size_t off = 0;
     auto put = [&](const std::vector<int> &v) {
@@ -1307,7 +1307,10 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
         return at;
     };
     const size_t o_bg = put(block_group), o_gf = put(group_first), o_gs = put(lay.gsize), o_gc = put(lay.gclass);
-    const size_t o_cb = put(class_begin), o_or = put(order);
+    // the group sizes that may take each class's units (all, unless given)
+    const std::vector<int> lo = gmin ? *gmin : std::vector<int>(nclasses, 1);
+    const std::vector<int> hi = gmax ? *gmax : std::vector<int>(nclasses, 1 << 30);
+    const size_t o_cb = put(class_begin), o_lo = put(lo), o_hi = put(hi), o_or = put(order);
     const size_t o_q = off, o_gu = off + 32 * (size_t)nclasses;
     DevBuf bu, bt, bw, bp, bb, bh, bc, btm;
     CK(cudaMalloc(&bu.p, sizeof(Params) * (size_t)nunits));
@@ -1334,6 +1337,8 @@ gadi_status run_batch(gadi_handle *h0, const void *k, size_t smem, std::vector<P
     B.group_size = ti + o_gs;
     B.group_class = ti + o_gc;
     B.class_begin = ti + o_cb;
+    B.class_gmin = ti + o_lo;
+    B.class_gmax = ti + o_hi;
     B.order = ti + o_or;
     B.queue = (int *)bt.p + o_q;
     B.group_unit = (int *)bt.p + o_gu;
@@ -1382,6 +1387,20 @@ std::map<std::vector<long long>, std::vector<double>> g_tune;
 
 // the key: grid, precision, options, blocks, and the class's alpha values
 // (alpha sets the inner iteration counts, hence the cost per outer iteration)
+// The resident H-solve on a group of s blocks: block b owns rows [b ny / s,
+// (b+1) ny / s) and keeps p of those rows plus a halo row on each side in
+// shared memory as floats.  A group may take a unit if each block owns a row
+// and its share fits the opt-in shared memory.
+size_t res_smem(long long nx, long long ny, int s)
+{
+    const long long rows = (ny + s - 1) / s;
+    return (size_t)(rows + 2) * (size_t)nx * sizeof(float);
+}
+bool res_allowed(long long nx, long long ny, int s, int optin)
+{
+    return s <= ny && res_smem(nx, ny, s) <= (size_t)optin;
+}
+
 std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts &o, int total,
                                 const std::vector<double> &alphas)
 {
@@ -1404,7 +1423,7 @@ std::vector<long long> tune_key(const gadi_handle *h, int prec, const gadi_opts 
 // Two runs (kTuneOuterA and kTuneOuterB outer iterations) give the time per
 // outer iteration by difference.  -1 for sizes above `total`.
 gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::vector<Params> &cls, int prec,
-                       int total, cudaStream_t st, std::vector<double> &t_outer, int nr = 1)
+                       int total, cudaStream_t st, std::vector<double> &t_outer, int nr = 1, int res_optin = 0)
 {
     const int nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
     t_outer.assign(nc, -1.0);
@@ -1414,6 +1433,11 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::ve
     for (int i = 0; i < nc; i++) {
         const int sz = kTuneSizes[i];
         if (sz > total) continue;
+        if (res_optin > 0) {
+            // the resident H-solve: sizes whose row share fits
+            if (!res_allowed(h->nx, h->ny, sz, res_optin)) continue;
+            smem = res_smem(h->nx, h->ny, sz);
+        }
         const int ng = total / sz;
         double med[2] = {0.0, 0.0};
         for (int run = 0; run < 2; run++) {
@@ -1453,14 +1477,6 @@ gadi_status tune_class(gadi_handle *h, const void *k, size_t smem, const std::ve
     return GADI_OK;
 }
 
-// The layout: one size per class and groups per class, every block used.
-// Size: fixed, or the tuned size with the fewest block-seconds per outer
-// iteration (s t(s); ties to the larger group, whose units finish sooner).
-// Groups: in proportion to the class's work, units x s t(s) x the grid's
-// side (the outer iteration count of HSS at alpha near alpha* grows with the
-// side), at least one group per class and no more groups than units; blocks
-// left over go, a group at a time, to the class with the longest estimated
-// finish.  Classes are in size order (largest first).
 // Groups per class for a given group size per class: in proportion to each
 // class's work (units x block-seconds per unit), at least one each, then one
 // at a time to the class that would finish last while the grid has room.
@@ -1513,6 +1529,11 @@ double finish_estimate(const std::vector<int> &g, const std::vector<double> &T, 
     return m;
 }
 
+// The layout: one size per class and groups per class, every block used.
+// Size: fixed, or (tuned) each class starts at the size with the fewest
+// block-seconds per unit and moves, one class at a time, to the size that
+// lowers the estimated finish time most.  Classes are in size order
+// (largest first).
 BatchLayout make_layout(const std::vector<long long> &side, const std::vector<int> &count,
                         const std::vector<std::vector<double>> &t_outer, int fixed, int total,
                         std::vector<int> *chosen, double *estimate)
@@ -1627,8 +1648,35 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     // vectors, FP32 inner solves), or a unit per right-hand side
     const bool inter = nrhs == 4 && prec == P_FP32 && o.u_r == GADI_FP64 && o.batch_interleave != 0;
     const int nr = inter ? 4 : 1;
-    const void *k = inter ? kernel_batched4_2d5(&smem) : kernel_batched_2d5(prec, vec ? 1 : 0, &smem, o.u_r == GADI_FP64X2);
+    // units with the SM-resident H-solve (p in shared memory): FP32 / BF16,
+    // 16-byte rows, an FP64 residual, opts->h_resident >= 1
+    bool res = !inter && vec && o.h_resident >= 1 && (prec == P_FP32 || prec == P_BF16) && o.u_r == GADI_FP64;
+    // the dynamic shared memory a block of the resident kernel may take: the
+    // opt-in limit less the kernel's static shared memory
+    int optin = 0;
+    if (res) {
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h0->device));
+        cudaFuncAttributes fa;
+        CK(cudaFuncGetAttributes(&fa, kernel_batched_2d5_res(prec)));
+        optin -= (int)fa.sharedSizeBytes;
+        res = optin > 0;
+    }
+    for (int i = 0; i < nsys && res; i++) {
+        // a fixed group size must suit every system; tuned, some candidate
+        // size must (else the batch takes the streaming H-solve)
+        bool any = false;
+        for (int sz : kTuneSizes)
+            if (o.batch_group > 0 ? sz == 1 && res_allowed(hs[i]->nx, hs[i]->ny, o.batch_group, optin)
+                                  : (o.max_blocks <= 0 || sz <= o.max_blocks) &&
+                                        res_allowed(hs[i]->nx, hs[i]->ny, sz, optin))
+                any = true;
+        res = any;
+    }
+    const void *k = inter ? kernel_batched4_2d5(&smem)
+                          : (res ? kernel_batched_2d5_res(prec)
+                                 : kernel_batched_2d5(prec, vec ? 1 : 0, &smem, o.u_r == GADI_FP64X2));
     if (!k) return GADI_ERR_UNSUPPORTED;
+    if (res) smem = (size_t)optin; // the occupancy at the largest share; each launch takes what it needs
     if (smem) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreadsHost, smem));
@@ -1700,13 +1748,14 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             }
             std::vector<long long> key = tune_key(hc, prec, o, total, al);
             key.push_back(nr);
+            key.push_back(res);
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 auto it = g_tune.find(key);
                 if (it != g_tune.end()) t_outer[c] = it->second;
             }
             if (t_outer[c].empty()) {
-                if ((s = tune_class(hc, k, smem, cls, prec, total, st, t_outer[c], nr)) != GADI_OK)
+                if ((s = tune_class(hc, k, smem, cls, prec, total, st, t_outer[c], nr, res ? optin : 0)) != GADI_OK)
                     return s;
                 std::lock_guard<std::mutex> lk(g_tune_mu);
                 g_tune[key] = t_outer[c];
@@ -1730,12 +1779,34 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
         }
         std::fprintf(stderr, "gadi batch layout: %d blocks, estimated finish %g s\n", lay.blocks, est);
     }
+    // resident units: the group sizes each class admits, and the shared
+    // memory of the largest share a group may take (its own class or, by
+    // stealing, a smaller one)
+    std::vector<int> gmin(ncl, 1), gmax(ncl, 1 << 30);
+    if (res) {
+        smem = 0;
+        for (int c = 0; c < ncl; c++) {
+            const gadi_handle *hc = hs[cls_sys[c]];
+            gmax[c] = (int)std::min<long long>(hc->ny, 1 << 30);
+            gmin[c] = 1 << 30;
+            // the share shrinks as the group grows: the smallest size that fits
+            for (int sz = 1; sz <= std::min(gmax[c], total) && gmin[c] == (1 << 30); sz++)
+                if (res_allowed(hc->nx, hc->ny, sz, optin)) gmin[c] = sz;
+        }
+        for (size_t g = 0; g < lay.gsize.size(); g++) {
+            const int sz = lay.gsize[g], c0 = lay.gclass[g];
+            if (sz < gmin[c0] || sz > gmax[c0]) return GADI_ERR_INVALID; // the tuner admits no such size
+            for (int c = c0; c < ncl; c++)
+                if (sz >= gmin[c] && sz <= gmax[c])
+                    smem = std::max(smem, res_smem(hs[cls_sys[c]]->nx, hs[cls_sys[c]]->ny, sz));
+        }
+    }
     const int hist_len = maxit + 2;
     std::vector<Ctl> hc;
     std::vector<unsigned long long> t0, t1;
     float ms = 0.f;
     if ((s = run_batch(h0, k, smem, units, class_begin, order, lay, max_n, prec, hist_len, st, hc, t0, t1, &ms,
-                       nr)) != GADI_OK)
+                       nr, &gmin, &gmax)) != GADI_OK)
         return s;
     gadi_status worst = GADI_OK;
     // (system, right-hand side) q = s * nrhs + j: its unit and control block
@@ -1755,7 +1826,7 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
             S.blocks = c.pad; // the size of the group that ran the unit
             S.alpha = alpha[q / nrhs];
             S.restarts = 0;
-            S.h_resident = 0;
+            S.h_resident = res ? 1 : 0;
             S.s_resident = 0;
             S.backward_err = -1.0;
         }

@@ -27,6 +27,9 @@ const void *kernel_batched_2d5(int prec, int vec, size_t *smem, int dd = 0);
 const void *kernel_batched_2d5_dd(int prec, int vec, size_t *smem);
 // the batched kernel with units of four interleaved right-hand sides (FP32)
 const void *kernel_batched4_2d5(size_t *smem);
+// the batched kernel whose units take the SM-resident H-solve (FP32 / BF16,
+// 16-byte rows; dynamic shared memory set by the caller)
+const void *kernel_batched_2d5_res(int prec);
 // record a message for gadi_last_error() on this thread
 void record_error(const char *msg);
 } // namespace gadi

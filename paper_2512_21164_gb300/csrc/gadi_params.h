@@ -151,6 +151,8 @@ struct BatchParams {
     const int *group_size;   // per group: blocks
     const int *group_class;  // per group: its size class
     const int *class_begin;  // per class c: its units are order[class_begin[c] .. class_begin[c+1])
+    const int *class_gmin;   // per class: the group sizes that may take its units are
+    const int *class_gmax;   // [class_gmin, class_gmax] (the resident H-solve's limits)
     const int *order;        // unit indices by class, largest system first within a class
     int *queue;      // per class (stride 32 ints): units taken so far (zeroed before launch)
     int *group_unit; // per group (stride 32 ints): the unit it is working on

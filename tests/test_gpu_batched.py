@@ -30,7 +30,12 @@ def _systems():
 
 @pytest.mark.parametrize("prec", [FP64, FP32, BF16])
 @pytest.mark.parametrize("group", [0, 1, 4])  # 0: tuned group sizes
-def test_batched_matches_oracle(prec, group):
+@pytest.mark.parametrize("hres", [None, 0])
+def test_batched_matches_oracle(prec, group, hres):
+    """hres None: the default options, under which FP32 and BF16 units take
+    the SM-resident H-solve (p of a block's rows in shared memory); 0: the
+    streaming H-solve.  The 40 x 8 system admits resident groups of at most
+    8 blocks, so with tuned sizes the larger groups may not take its units."""
     import torch
     nrhs = 2
     systems = _systems()
@@ -45,9 +50,11 @@ def test_batched_matches_oracle(prec, group):
         xs.append(torch.zeros(nrhs * p.nvec, dtype=torch.float64, device="cuda"))
         alphas.append(a)
     tol_in = 1e-2 if prec == BF16 else 1e-3
+    kw = {} if hres is None else dict(h_resident=hres)
     st, stats = G.solve_batched(handles, nrhs, bs, xs, alphas, 1.0, prec, 1e-10, 3000,
-                                tol_h=tol_in, tol_s=tol_in, batch_group=group)
+                                tol_h=tol_in, tol_s=tol_in, batch_group=group, **kw)
     assert st == G.OK, G.status_str(st)
+    resident = hres is None and prec != FP64
     for s, (p, a) in enumerate(systems):
         orc = O.Oracle(p)
         xg_all = xs[s].cpu().numpy()
@@ -63,6 +70,9 @@ def test_batched_matches_oracle(prec, group):
             assert rel <= 1e-10
             assert u["seconds"] > 0
             assert u["blocks"] == group if group > 0 else 1 <= u["blocks"] <= 64
+            assert u["h_resident"] == (1 if resident else 0)
+            if resident:
+                assert u["blocks"] <= p.ny
     for h in handles:
         h.close()
 
