@@ -76,7 +76,8 @@ struct CsrImpl {
     // gathers are independent loads, so a thread keeps RB rows' loads in
     // flight instead of one chain of dependent loads.  Each row still sums
     // its entries in CSR order.  body(row, sum) consumes each row's result.
-    static constexpr int RB = 4;
+    // (2048^2 as CSR: 4 rows 10.08 s, 6 rows 9.82 s, 8 rows 9.99 s)
+    static constexpr int RB = 6;
     template <class VT, class XT, class AR, class VP, class Body>
     __device__ void spmv_loop(const int *rp, const int *cl, const VP *val, const XT *x, Body body) const
     {
