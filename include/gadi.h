@@ -342,6 +342,20 @@ gadi_status gadi_probe_fp64(int iters, double *gops, double *sm_ops_per_clk);
  * on the legacy default stream.  Errors: INVALID (n < 0, null pointers), CUDA. */
 gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches);
 
+/* The layout rule of gadi_solve_batched on given timings, host only (no
+ * GPU): ncl size classes, largest systems first, class c with count[c] units
+ * on a grid of side side[c]; t_outer[c * 7 + i] the seconds per outer
+ * iteration of one of its units on a group of 2^i blocks (i = 0..6; <= 0 =
+ * not timed / not admitted); fixed > 0 = every class on groups of min(fixed,
+ * total) blocks; total = blocks of the grid.  Out: size[c] blocks per group
+ * and groups[c] groups of class c (every class >= 1 group, groups[c] <=
+ * count[c], sum of size x groups <= total), *estimate the estimated finish
+ * time (max over classes of ceil(count / groups) x t(size) x side).
+ * Errors: INVALID (bad arguments, a class without a timed size, or more
+ * classes than fit in the grid). */
+gadi_status gadi_batch_plan(int ncl, const long long *side, const int *count, const double *t_outer, int fixed,
+                            int total, int *size, int *groups, double *estimate);
+
 /* y = Op x in FP64 for Op in {A, M, N, A^T} (Sec. 3.1 splitting).  x and y
  * may be host or device memory; stream as in gadi_opts (NULL = default). */
 gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream);

@@ -115,6 +115,10 @@ def lib():
             L.gadi_probe_fp64.restype = C.c_int
             L.gadi_selftest_convert.argtypes = [vp, C.c_longlong, C.POINTER(C.c_longlong)]
             L.gadi_selftest_convert.restype = C.c_int
+            L.gadi_batch_plan.argtypes = [C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.gadi_batch_plan.restype = C.c_int
             L.gadi_solve_h_2d_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, vp, vp,
                                                   C.c_double, C.c_int, C.c_int, ip, vp]
             for f in ("gadi_create", "gadi_solve", "gadi_apply", "gadi_norm2_estimate",
@@ -316,6 +320,31 @@ def probe_fp64(iters=200000):
     if st != OK:
         raise GadiError(st, "gadi_probe_fp64")
     return g.value, r.value
+
+
+# the candidate group sizes of the batched solve's tuner (2^i blocks)
+BATCH_SIZES = (1, 2, 4, 8, 16, 32, 64)
+
+
+def batch_plan(side, count, t_outer=None, fixed=0, total=152):
+    """gadi_batch_plan (host only): the batched solve's layout for size classes
+    (largest first) with grid sides `side`, unit counts `count` and per-class
+    seconds per outer iteration on groups of BATCH_SIZES blocks (`t_outer`,
+    ncl x 7; <= 0 = not admitted).  Returns (sizes, groups, estimate)."""
+    n = len(side)
+    sd = (C.c_longlong * n)(*[int(v) for v in side])
+    cn = (C.c_int * n)(*[int(v) for v in count])
+    t = None
+    if t_outer is not None:
+        flat = [float(v) for row in t_outer for v in row]
+        if len(flat) != 7 * n:
+            raise ValueError("t_outer: 7 timings per class")
+        t = (C.c_double * len(flat))(*flat)
+    sz, gr, est = (C.c_int * n)(), (C.c_int * n)(), C.c_double()
+    st = lib().gadi_batch_plan(n, sd, cn, t, int(fixed), int(total), sz, gr, C.byref(est))
+    if st != OK:
+        raise GadiError(st, "gadi_batch_plan")
+    return list(sz), list(gr), est.value
 
 
 def selftest_convert(d):

@@ -1834,6 +1834,33 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     return worst;
 }
 
+gadi_status gadi_batch_plan(int ncl, const long long *side, const int *count, const double *t_outer, int fixed,
+                            int total, int *size, int *groups, double *estimate)
+{
+    constexpr int nc = (int)(sizeof kTuneSizes / sizeof kTuneSizes[0]);
+    if (ncl <= 0 || !side || !count || !size || !groups || total <= 0 || (fixed <= 0 && !t_outer))
+        return GADI_ERR_INVALID;
+    std::vector<long long> sd(side, side + ncl);
+    std::vector<int> cn(count, count + ncl);
+    std::vector<std::vector<double>> t(ncl, std::vector<double>(nc, -1.0));
+    for (int c = 0; c < ncl; c++) {
+        if (sd[c] <= 0 || cn[c] <= 0) return GADI_ERR_INVALID;
+        if (t_outer)
+            for (int i = 0; i < nc; i++) t[c][i] = t_outer[(size_t)c * nc + i];
+    }
+    std::vector<int> chosen;
+    double est = 0.0;
+    const BatchLayout lay = make_layout(sd, cn, t, fixed, total, &chosen, &est);
+    if (lay.blocks <= 0) return GADI_ERR_INVALID;
+    for (int c = 0; c < ncl; c++) {
+        size[c] = chosen[c];
+        groups[c] = 0;
+    }
+    for (int g : lay.gclass) groups[g]++;
+    if (estimate) *estimate = est;
+    return GADI_OK;
+}
+
 gadi_status gadi_apply(gadi_handle *h, gadi_op op, const double *x, double *y, void *stream)
 {
     if (!h || !x || !y || op < GADI_OP_A || op > GADI_OP_AT || x == y) return GADI_ERR_INVALID;
