@@ -336,8 +336,9 @@ gadi_status gadi_probe_fp64(int iters, double *gops, double *sm_ops_per_clk);
  * (2) binary64 -> BF16 round-to-nearest-even, both against the hardware
  * conversion, and (3) binary32 -> binary64 of the float whose bits are the
  * low 32 bits of the input, against the hardware widening, and (4) that
- * float -> BF16 by the conversion instruction equals the integer rounding
- * sequence (non-NaN floats) -- all bit for bit.  mismatches (HOST array of
+ * float -> BF16 by the conversion instruction, one value and two values
+ * (with the float of the upper 32 bits) per instruction, equals the integer
+ * rounding sequence (non-NaN floats) -- all bit for bit.  mismatches (HOST array of
  * 4) receives the count per check.  Synchronous
  * on the legacy default stream.  Errors: INVALID (n < 0, null pointers), CUDA. */
 gadi_status gadi_selftest_convert(const double *in, long long n, long long *mismatches);

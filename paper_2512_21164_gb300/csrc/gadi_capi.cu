@@ -498,6 +498,19 @@ __global__ void k_selftest_convert(const double *in, long long n, unsigned long 
         const float g = __uint_as_float((uint32_t)__double_as_longlong(d));
         if (__double_as_longlong(f32_to_f64_fast(g)) != __double_as_longlong((double)g)) atomicAdd(bad + 2, 1ull);
         if (!isnan(g) && f32_to_bf16_cvt(g) != f32_to_bf16(g)) atomicAdd(bad + 3, 1ull);
+        // the pair form (two roundings by one instruction): g with the float
+        // of the upper 32 bits of d, in both positions of the pair
+        const float g2 = __uint_as_float((uint32_t)((unsigned long long)__double_as_longlong(d) >> 32));
+        if (!isnan(g) && !isnan(g2)) {
+            float a, b;
+            f32x2_round_bf16(g, g2, a, b);
+            const bool ok1 = __float_as_uint(a) == (uint32_t)f32_to_bf16(g) << 16 &&
+                             __float_as_uint(b) == (uint32_t)f32_to_bf16(g2) << 16;
+            f32x2_round_bf16(g2, g, a, b);
+            const bool ok2 = __float_as_uint(a) == (uint32_t)f32_to_bf16(g2) << 16 &&
+                             __float_as_uint(b) == (uint32_t)f32_to_bf16(g) << 16;
+            if (!ok1 || !ok2) atomicAdd(bad + 3, 1ull);
+        }
     }
 }
 

@@ -40,6 +40,17 @@ __device__ __forceinline__ uint16_t f32_to_bf16_cvt(float f)
     return (uint16_t)h;
 }
 
+// two floats rounded to BF16 (nearest even) by one instruction and returned
+// as floats: `hi` from the upper half of the packed pair, `lo` the lower.  The
+// same rounding as f32_to_bf16_cvt for each value.
+__device__ __forceinline__ void f32x2_round_bf16(float a, float b, float &ra, float &rb)
+{
+    unsigned d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(a), "f"(b));
+    ra = __uint_as_float(d & 0xffff0000u);
+    rb = __uint_as_float(d << 16);
+}
+
 // double -> BF16 without double rounding: round to odd at binary32 (truncate,
 // then set the last bit if anything was discarded), then round to nearest
 // even at BF16.  Binary32 carries 16 more significand bits than BF16, so the

@@ -155,6 +155,20 @@ struct FieldX {
     }
 };
 
+// fl_s(a), fl_s(b) as values of the compute type: for BF16 the two roundings
+// by one instruction (the same round-to-nearest-even as one at a time)
+template <int PREC, class C>
+__device__ __forceinline__ void round_pair(C a, C b, C &ra, C &rb)
+{
+    using PT = Prec<PREC>;
+    if constexpr (PREC == P_BF16) {
+        f32x2_round_bf16(a, b, ra, rb);
+    } else {
+        ra = PT::ld(PT::st(a));
+        rb = PT::ld(PT::st(b));
+    }
+}
+
 // fl_s(src + beta p_old) (the CG direction update), or src on the first step
 template <int PREC>
 struct FieldDir {
@@ -176,9 +190,22 @@ struct FieldDir {
     }
     template <int N> __device__ void value(const Raw<N> &r, C (&o)[N]) const
     {
+        if constexpr (PREC == P_BF16 && N % 2 == 0) {
 #pragma unroll
-        for (int v = 0; v < N; v++)
-            o[v] = first ? PT::ld(r.s[v]) : PT::ld(PT::st(A::madd(beta, PT::ld(r.p[v]), PT::ld(r.s[v]))));
+            for (int v = 0; v < N; v += 2) {
+                if (first) {
+                    o[v] = PT::ld(r.s[v]);
+                    o[v + 1] = PT::ld(r.s[v + 1]);
+                } else {
+                    round_pair<PREC>(A::madd(beta, PT::ld(r.p[v]), PT::ld(r.s[v])),
+                                     A::madd(beta, PT::ld(r.p[v + 1]), PT::ld(r.s[v + 1])), o[v], o[v + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < N; v++)
+                o[v] = first ? PT::ld(r.s[v]) : PT::ld(PT::st(A::madd(beta, PT::ld(r.p[v]), PT::ld(r.s[v]))));
+        }
     }
     // shared-memory staging (march_smem): field vector k, whether it is read
     static constexpr int NF = 2;
@@ -210,10 +237,16 @@ struct FieldLoad {
     template <int N> __device__ void load(long long g, Raw<N> &r) const { VecIO<S, N>::load_ca(src + g, r.s); }
     template <int N> __device__ void value(const Raw<N> &r, C (&o)[N]) const
     {
+        if constexpr (SCALE && PREC == P_BF16 && N % 2 == 0) {
 #pragma unroll
-        for (int v = 0; v < N; v++) {
-            if constexpr (SCALE) o[v] = PT::ld(PT::st(A::mul(scale, PT::ld(r.s[v]))));
-            else o[v] = PT::ld(r.s[v]);
+            for (int v = 0; v < N; v += 2)
+                round_pair<PREC>(A::mul(scale, PT::ld(r.s[v])), A::mul(scale, PT::ld(r.s[v + 1])), o[v], o[v + 1]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < N; v++) {
+                if constexpr (SCALE) o[v] = PT::ld(PT::st(A::mul(scale, PT::ld(r.s[v]))));
+                else o[v] = PT::ld(r.s[v]);
+            }
         }
     }
     static constexpr int NF = 1;
@@ -1452,10 +1485,10 @@ struct StencilImpl {
                                             PT::ld(rv[u][v + 3]));
                         } else {
                             t = d4[v / 4];
-                            t.x = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[u][v]))));
-                            t.y = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[u][v + 1]))));
-                            t.z = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[u][v + 2]))));
-                            t.w = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[u][v + 3]))));
+                            round_pair<PREC>(A2::madd(beta, t.x, PT::ld(rv[u][v])),
+                                             A2::madd(beta, t.y, PT::ld(rv[u][v + 1])), t.x, t.y);
+                            round_pair<PREC>(A2::madd(beta, t.z, PT::ld(rv[u][v + 2])),
+                                             A2::madd(beta, t.w, PT::ld(rv[u][v + 3])), t.z, t.w);
                         }
                         d4[v / 4] = t;
                     }
@@ -1696,10 +1729,10 @@ struct StencilImpl {
                 t = make_float4(PT::ld(rv[v]), PT::ld(rv[v + 1]), PT::ld(rv[v + 2]), PT::ld(rv[v + 3]));
             } else {
                 t = d4[v / 4];
-                t.x = PT::ld(PT::st(A2::madd(beta, t.x, PT::ld(rv[v]))));
-                t.y = PT::ld(PT::st(A2::madd(beta, t.y, PT::ld(rv[v + 1]))));
-                t.z = PT::ld(PT::st(A2::madd(beta, t.z, PT::ld(rv[v + 2]))));
-                t.w = PT::ld(PT::st(A2::madd(beta, t.w, PT::ld(rv[v + 3]))));
+                round_pair<PREC>(A2::madd(beta, t.x, PT::ld(rv[v])), A2::madd(beta, t.y, PT::ld(rv[v + 1])), t.x,
+                                 t.y);
+                round_pair<PREC>(A2::madd(beta, t.z, PT::ld(rv[v + 2])), A2::madd(beta, t.w, PT::ld(rv[v + 3])), t.z,
+                                 t.w);
             }
             d4[v / 4] = t;
         }
@@ -2029,10 +2062,8 @@ struct StencilImpl {
 #pragma unroll
         for (int v = 0; v < W; v += 4) {
             float4 t;
-            t.x = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v]))));
-            t.y = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 1]))));
-            t.z = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 2]))));
-            t.w = PT::ld(PT::st(A2::mul(gamma, PT::ld(zv[v + 3]))));
+            round_pair<PREC>(A2::mul(gamma, PT::ld(zv[v])), A2::mul(gamma, PT::ld(zv[v + 1])), t.x, t.y);
+            round_pair<PREC>(A2::mul(gamma, PT::ld(zv[v + 2])), A2::mul(gamma, PT::ld(zv[v + 3])), t.z, t.w);
             d4[v / 4] = t;
         }
     }
