@@ -1,0 +1,193 @@
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py
+times (default options, one block per SM).
+
+The oracle cannot run Algorithm 1 to 1e-10 on 4.2 M or 134 M points within a
+test, so at full size the checks are of two kinds:
+
+* outputs the oracle computes directly: the residual step (x + y, b - A x in
+  FP64, the cast to u_s, the norm) on the whole 2048^2 grid, the whole 512^3
+  grid and the whole 4096^2 complex grid, bit for bit;
+* properties that hold at any size, checked with the oracle's FP64 operator on
+  the full grid: the returned iterate's relative residual is the one the solve
+  reports and is <= 1e-10, its normwise backward error (eq. 3.2, with a lower
+  bound on ||A||_2, which bounds it from above) is <= 1e-10, and the forward
+  error is what the conditioning allows.  The batched solve (96 systems x 4 right-hand sides) is
+  checked unit by unit the same way, each unit's reported relres against the
+  oracle's residual of its returned iterate.
+
+Inputs are the benchmark's: the seeded grids of `workloads.config2/3/4/5`,
+b = A x_true by the oracle."""
+import numpy as np
+import pytest
+
+import bench
+import oracle as O
+import paper_2512_21164_gb300 as G
+from helpers import BF16, FP32, FP64, dev64, us_empty, us_to_device, us_to_host
+from workloads import SplitMix64, alpha_star, config2, config3, config4, config5
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2512_21164_gb300 import build
+    build.build()
+
+
+def _rnd(prec, a):
+    """Values representable in u_s (the same values go to both sides)."""
+    if prec == FP64:
+        return np.asarray(a, np.float64)
+    if prec == FP32:
+        return np.asarray(a, np.float32).astype(np.float64)
+    from helpers import bf16_from_bits
+    # truncate the binary32 pattern to its upper 16 bits
+    bits = (np.asarray(a, np.float32).view(np.uint32) >> np.uint32(16)).astype(np.uint16)
+    return bf16_from_bits(bits)
+
+
+def _residual_full(p, prec, seed):
+    """The residual step on the whole grid against the oracle, bit for bit."""
+    import torch
+    orc = O.Oracle(p)
+    m = p.nvec
+    g = SplitMix64(seed)
+    x = g.uniform_array(m) - 0.5
+    b = orc.rhs(g.uniform_array(m))
+    y = _rnd(prec, (g.uniform_array(m) - 0.5) * 1e-2)
+    with G.Gadi.from_problem(p) as H:
+        xo = torch.zeros(m, dtype=torch.float64, device="cuda")
+        ro = torch.zeros_like(xo)
+        rs = us_empty(m, prec)
+        nrm = H.step_residual(prec, dev64(b), dev64(x), us_to_device(y, prec), xo, ro, rs)
+        torch.cuda.synchronize()
+        xo_h, ro_h, rs_h = xo.cpu().numpy(), ro.cpu().numpy(), us_to_host(rs, prec)
+        del xo, ro, rs
+    xo_o, r_o, rs_o, n_o = orc.residual(prec, b, x, y)
+    assert np.array_equal(xo_h, xo_o)
+    assert np.array_equal(ro_h, r_o)
+    assert np.array_equal(rs_h, rs_o)
+    assert abs(nrm - n_o) <= 1e-12 * n_o
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_c2_residual_step_full_grid(prec):
+    p, _ = config2()
+    _residual_full(p, prec, 31)
+
+
+def test_c3_residual_step_full_grid():
+    p, _ = config3()
+    _residual_full(p, BF16, 32)
+
+
+def test_c4_residual_step_full_grid():
+    p, _ = config4()
+    _residual_full(p, FP32, 33)
+
+
+def _check_solution(p, b, x_np, stats, xt, fe_max):
+    """relres of the returned iterate by the oracle's FP64 operator, against
+    the reported one and 1e-10; backward error (eq. 3.2) <= 1e-10 with ||A||_2
+    bounded below by ||A x_true|| / ||x_true|| (a lower bound on ||A|| bounds
+    the backward error from above); forward error."""
+    orc = O.Oracle(p)
+    r = b - orc.apply(O.OP_A, x_np)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1e-10, rel
+    assert abs(rel - stats["relres"]) <= 1e-6 * rel, (rel, stats["relres"])
+    Anorm_lo = np.linalg.norm(b) / np.linalg.norm(xt)
+    be = O.backward_error(np.linalg.norm(r), Anorm_lo, x_np, b)
+    assert be <= 1e-10, be
+    fe = np.linalg.norm(x_np - xt) / np.linalg.norm(xt)
+    assert fe <= fe_max, fe
+    return rel, be, fe
+
+
+def test_c2_full_solve_benchmark_configuration():
+    """2048^2, alpha = 8 alpha*, omega = 0, FP32 inner solves with inner
+    tolerances 1e-3: the headline solve, on the kernel the benchmark times
+    (z, r of the H-solve in tensor memory, CGNR resident, 152 blocks)."""
+    import torch
+    p, xt = config2()
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    alpha = bench.ALPHA_FACTOR * alpha_star(p)
+    x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+    with G.Gadi.from_problem(p) as H:
+        st, s = H.solve(dev64(b), x, alpha, bench.OMEGA, FP32, bench.TOL, bench.MAXIT,
+                        tol_h=bench.TOL_H, tol_s=bench.TOL_S)
+    assert st == G.OK, G.status_str(st)
+    assert s["h_resident"] == 2 and s["s_resident"] == 1, s
+    # kappa(A) ~ 1e6 here: a relative forward error of 1e-10 x kappa bounds it
+    _check_solution(p, b, x.cpu().numpy(), s, xt, 1e-4)
+
+
+def test_c3_full_solve_bf16():
+    """512^3, alpha = alpha*, omega = 0, BF16 inner solves with inner
+    tolerances 1e-2 (the benchmark's 512^3 BF16 line)."""
+    import torch
+    p, xt = config3()
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+    with G.Gadi.from_problem(p) as H:
+        st, s = H.solve(dev64(b), x, alpha_star(p), 0.0, BF16, 1e-10, bench.MAXIT, tol_h=1e-2, tol_s=1e-2)
+    assert st == G.OK, G.status_str(st)
+    x_np = x.cpu().numpy()
+    del x
+    _check_solution(p, b, x_np, s, xt, 1e-4)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32, BF16])
+def test_c4_full_solve(prec):
+    """4096^2 complex reaction-diffusion, alpha = alpha*, omega = 1 (the
+    benchmark's config-4 lines)."""
+    import torch
+    p, xt = config4()
+    orc = O.Oracle(p)
+    b = orc.rhs(xt)
+    x = torch.zeros(p.nvec, dtype=torch.float64, device="cuda")
+    tin = 1e-2 if prec == BF16 else 1e-3
+    with G.Gadi.from_problem(p) as H:
+        st, s = H.solve(dev64(b), x, alpha_star(p), 1.0, prec, 1e-10, bench.MAXIT, tol_h=tin, tol_s=tin)
+    assert st == G.OK, G.status_str(st)
+    _check_solution(p, b, x.cpu().numpy(), s, xt, 1e-6)
+
+
+def test_c5_full_batch_units_report_their_residual():
+    """The 96-system, 4-right-hand-side batch with the benchmark's literal
+    alpha values and options (tuned groups, resident units), capped at 150
+    outer iterations: every unit's reported relres is the relative residual
+    of the iterate it returned (checked by the oracle), and the unit's status
+    agrees with it."""
+    import torch
+    systems = config5(96, 4)
+    hs, bs, xs, al, rhs = [], [], [], [], []
+    for p, a, xts in systems:
+        orc = O.Oracle(p)
+        bb = np.concatenate([orc.rhs(xts[j]) for j in range(4)])
+        rhs.append(bb)
+        hs.append(G.Gadi.from_problem(p))
+        bs.append(dev64(bb))
+        xs.append(torch.zeros(4 * p.nvec, dtype=torch.float64, device="cuda"))
+        al.append(a)
+    st, stats = G.solve_batched(hs, 4, bs, xs, al, bench.OMEGA, FP32, bench.TOL, 150,
+                                tol_h=bench.TOL_INNER, tol_s=bench.TOL_INNER, check=False)
+    assert st >= 0, G.status_str(st)
+    for s_, (p, a, xts) in enumerate(systems):
+        orc = O.Oracle(p)
+        xg = xs[s_].cpu().numpy()
+        for j in range(4):
+            u = stats[s_ * 4 + j]
+            b = rhs[s_][j * p.nvec:(j + 1) * p.nvec]
+            r = b - orc.apply(O.OP_A, xg[j * p.nvec:(j + 1) * p.nvec])
+            rel = np.linalg.norm(r) / np.linalg.norm(b)
+            assert abs(rel - u["relres"]) <= 1e-6 * rel + 1e-300, (s_, j, rel, u["relres"])
+            if u["status"] == G.OK:
+                assert rel <= 1e-10
+            else:
+                assert u["status"] in (G.NOT_CONVERGED, G.STAGNATED) and u["outer_its"] <= 150
+    for h in hs:
+        h.close()
