@@ -6,7 +6,8 @@ test, so at full size the checks are of two kinds:
 
 * outputs the oracle computes directly: the residual step (x + y, b - A x in
   FP64, the cast to u_s, the norm) on the whole 2048^2 grid, the whole 512^3
-  grid and the whole 4096^2 complex grid, bit for bit;
+  grid and the whole 4096^2 complex grid, and one CG step on H on exact
+  inputs over the whole 2048^2 and 512^3 grids, bit for bit;
 * properties that hold at any size, checked with the oracle's FP64 operator on
   the full grid: the returned iterate's relative residual is the one the solve
   reports and is <= 1e-10, its normwise backward error (eq. 3.2, with a lower
@@ -191,3 +192,36 @@ def test_c5_full_batch_units_report_their_residual():
                 assert u["status"] in (G.NOT_CONVERGED, G.STAGNATED) and u["outer_its"] <= 150
     for h in hs:
         h.close()
+
+
+def _sparse_dyadic(m, nonzero, kmax, seed):
+    """k/8 with k uniform in [-kmax, kmax] \\ {0} at `nonzero` random positions."""
+    g = SplitMix64(seed)
+    v = np.zeros(m)
+    for _ in range(nonzero):
+        k = 0
+        while k == 0:
+            k = int(g.uniform() * (2 * kmax + 1)) - kmax
+        v[int(g.uniform() * m)] = k / 8.0
+    return v
+
+
+@pytest.mark.parametrize("which,prec", [("c2", FP32), ("c2", BF16), ("c3", BF16), ("c3", FP32)])
+def test_h_step_full_grid_same_bits_on_exact_inputs(which, prec):
+    """One CG step on H = alpha I + M at full size, through the kernel the
+    solves take there (2048^2 FP32: z and r in tensor memory; 512^3: the plane
+    ring): rs = k/8 (|k| <= 7) at 4000 points and alpha = 1/4 make H p and both
+    dot products exact in FP32, so z = fl(a p) must be the oracle's bit for
+    bit over the whole grid."""
+    import torch
+    p, _ = config2() if which == "c2" else config3()
+    rs = _sparse_dyadic(p.nvec, 4000, 7, 503)
+    with G.Gadi.from_problem(p) as H:
+        z = us_empty(p.nvec, prec)
+        its = H.step_solve_h(0.25, prec, us_to_device(rs, prec), z, 0.0, 1, 0)
+        torch.cuda.synchronize()
+        zg = us_to_host(z, prec)
+        del z
+    zo, it_o = O.Oracle(p).solve_h(0.25, prec, rs, 0.0, 1, 0)
+    assert its == it_o == 1
+    assert np.array_equal(zg, zo), np.max(np.abs(zg - zo))
