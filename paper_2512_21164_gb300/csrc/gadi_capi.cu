@@ -1677,13 +1677,14 @@ gadi_status gadi_solve_batched(gadi_handle *const *hs, int nsys, int nrhs, const
     for (int i = 0; i < nsys && res; i++) {
         // a fixed group size must suit every system; tuned, some candidate
         // size must (else the batch takes the streaming H-solve)
-        bool any = false;
-        for (int sz : kTuneSizes)
-            if (o.batch_group > 0 ? sz == 1 && res_allowed(hs[i]->nx, hs[i]->ny, o.batch_group, optin)
-                                  : (o.max_blocks <= 0 || sz <= o.max_blocks) &&
-                                        res_allowed(hs[i]->nx, hs[i]->ny, sz, optin))
-                any = true;
-        res = any;
+        if (o.batch_group > 0) {
+            res = res_allowed(hs[i]->nx, hs[i]->ny, o.batch_group, optin);
+        } else {
+            bool any = false;
+            for (int sz : kTuneSizes)
+                any = any || ((o.max_blocks <= 0 || sz <= o.max_blocks) && res_allowed(hs[i]->nx, hs[i]->ny, sz, optin));
+            res = any;
+        }
     }
     const void *k = inter ? kernel_batched4_2d5(&smem)
                           : (res ? kernel_batched_2d5_res(prec)
