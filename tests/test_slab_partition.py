@@ -1,4 +1,4 @@
-"""Slab partitioning of one system over two ranks (gloo on CPU): the plan,
+"""Slab partitioning of one system over two and three ranks (gloo on CPU): the plan,
 the halo exchange and the partitioned operator products reproduce the
 undivided grid's products bit for bit, and a partitioned CG on H (one halo
 exchange per product, two all-reduces per iteration) matches the oracle's CG.
@@ -124,14 +124,16 @@ def _rank_main(rank, world, port, results):
     results[rank] = out
 
 
-def test_two_ranks_reproduce_the_undivided_grid():
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_reproduce_the_undivided_grid(world):
+    """world = 3: the middle rank exchanges ghost planes with both neighbours."""
     import torch.multiprocessing as mp
     port = _free_port()
     mgr = mp.get_context("spawn").Manager()
     results = mgr.dict()
-    mp.spawn(_rank_main, args=(2, port, results), nprocs=2, join=True)
-    assert set(results.keys()) == {0, 1}
-    for rank in (0, 1):
+    mp.spawn(_rank_main, args=(world, port, results), nprocs=world, join=True)
+    assert set(results.keys()) == set(range(world))
+    for rank in range(world):
         res = dict(results[rank])
         for key, ok in res.items():
             if isinstance(key, tuple):
